@@ -1,0 +1,331 @@
+"""Benchmark: Lanczos probe-steps/s of the preconditioned eigenvalue-count
+estimator on one GB300, FP32-mixed (headline) and FP64, with the HBM
+roofline of the dominant kernel and the FP64 CPU oracle timed beside it.
+
+Workload (default): FD Hamiltonian H = -1/2 Lap_h + V, 7-point periodic 64^3
+(n = 262,144), h = 0.3, 32 Gaussian wells; shifts lambda_min - 1 and eta;
+Chebyshev degree-8 kinetic preconditioner; 64 Rademacher probes per shift;
+30 Lanczos steps.  One benchmark step = one full count (2 shifts x 64 probes x
+30 Lanczos steps, every kernel of the path) with the matrix resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): the path shards by probe columns with no data
+exchange; every rank runs its own replica on its own probes (seed + rank)
+and the job reports the sum of all ranks' probe-steps over the slowest
+rank's time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "probe Lanczos steps/s + HBM GB/s, FP32-mixed vs FP64 at count error <=0.5"
+UNIT = "probe-steps/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _make_ctx(evc, W, precision, stream_ptr, V=None):
+    if W.kind == "stencil":
+        ctx = evc.Context.stencil(W.N, W.h, W.order, W.potential() if V is None else V,
+                                  precision=precision, stream=stream_ptr)
+    else:
+        ctx = evc.Context.csr(W.csr(), precision=precision, stream=stream_ptr)
+    kind = {"identity": evc.EVC_PREC_IDENTITY, "jacobi": evc.EVC_PREC_JACOBI,
+            "cheb": evc.EVC_PREC_CHEB_KINETIC}[W.precond]
+    ctx.set_precond(kind, *W.prec_params)
+    ctx.reserve(len(W.shifts), W.nprobe, W.maxsteps)
+    return ctx
+
+
+def _stencil_roofline(evc, recs, peak, peak_kind):
+    st = [r for r in recs if r[0] == evc.EVC_K_STENCIL and r[2] > 0]
+    if not st:
+        return None, {}
+    ms = np.array([r[2] for r in st])
+    by = np.array([r[3] for r in st])
+    ach = by.sum() / (ms.sum() * 1e-3) / 1e9            # GB/s over all stencil passes
+    per_kind = {}
+    for k, name in enumerate(evc.KERNEL_NAMES):
+        rr = [r for r in recs if r[0] == k and r[2] > 0]
+        if rr:
+            t = sum(r[2] for r in rr)
+            b = sum(r[3] for r in rr)
+            per_kind[name] = {"launches": len(rr), "ms": round(t, 4),
+                              "GB/s": round(b / (t * 1e-3) / 1e9, 1) if t > 0 else None}
+    roof = {"bound": "hbm", "kernel": "stencil_pass_kernel", "achieved": round(ach, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "peak_source": peak_kind, "traffic": None,
+            "bytes_per_launch_avg": float(by.mean()), "ms_per_launch_avg": float(ms.mean()),
+            "launches": len(st)}
+    return roof, per_kind
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1602_02306_gb300 import evc, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    evc.load()
+    W = workloads.WORKLOADS[args.workload]()
+    S, m, k = len(W.shifts), W.nprobe, W.maxsteps
+    seed = args.seed + rank
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(ctx, steps, warmup, profile):
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 1 if profile else 0)
+        dq = torch.empty(S * m, dtype=torch.float64, device="cuda")
+        dL = torch.empty(S, dtype=torch.float64, device="cuda")
+        ds = torch.empty(S, dtype=torch.int32, device="cuda")
+        for _ in range(warmup):
+            evc.evc_count_slices_async(ctx.h, W.shifts, m, k, W.tol, seed, dL.data_ptr(),
+                                       dq.data_ptr(), ds.data_ptr())
+        evc.evc_sync(ctx.h)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            evc.evc_count_slices_async(ctx.h, W.shifts, m, k, W.tol, seed, dL.data_ptr(),
+                                       dq.data_ptr(), ds.data_ptr())
+        e1.record(stream)
+        evc.evc_sync(ctx.h)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        return ms, dL.cpu().numpy(), ds.cpu().numpy()
+
+    # ---- headline: FP32-mixed, inputs resident
+    ctx = _make_ctx(evc, W, evc.EVC_MIXED, sp)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mixed, L_mixed, steps_mixed = timed(ctx, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    recs = evc.evc_get_profile(ctx.h)
+    launches_per_step = len(recs)
+    roof, per_kind = _stencil_roofline(evc, recs, peak, peak_kind)
+    # ---- e2e: host V (pinned) -> device, count, per-probe results -> host
+    Vh = torch.from_numpy(W.potential().astype(np.float32)).pin_memory() if W.kind == "stencil" else None
+    evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
+    t_e2e = None
+    if not args.skip_e2e:
+        evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            if Vh is not None:
+                evc.evc_set_values(ctx.h, Vh.data_ptr(), False)
+            evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
+        t_e2e = time.perf_counter() - t0
+        barrier()
+    h2d = W.n * 4 if Vh is not None else 0
+    d2h = S * m * 8 + S * 8 + S * 4
+    ctx.close()
+    # ---- FP64 path on the same GPU
+    ms_fp64, L_fp64 = None, None
+    if not args.skip_fp64:
+        ctx64 = _make_ctx(evc, W, evc.EVC_FP64, sp)
+        ms_fp64, L_fp64, steps_fp64 = timed(ctx64, max(1, args.steps // 2), 1, profile=False)
+        ctx64.close()
+
+    psteps = float(S * m * k)          # probe-steps per count (tol = 0: all columns run k steps)
+    t_step = ms_mixed / args.steps
+    t_max = t_step
+    e2e_t = (t_e2e / args.steps) if t_e2e is not None else float("nan")
+    if world > 1:
+        t = torch.tensor([t_step, e2e_t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_t = float(t[0]), float(t[1])
+    value = world * psteps / (t_max * 1e-3)
+    est_mixed = float(L_mixed[1] - L_mixed[0]) if S == 2 else None
+    est_fp64 = float(L_fp64[1] - L_fp64[0]) if (S == 2 and L_fp64 is not None) else None
+    fp64_steps = max(1, args.steps // 2)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": W.name, "n": W.n, "shifts": S, "probes_per_shift": m,
+                   "lanczos_steps": k, "precond": "chebyshev-8 kinetic (c=1)",
+                   "precision": "FP32 vectors/operator, FP64 alpha/beta/reorth coefficients/eig",
+                   "step": "one full count: all shifts x probes x Lanczos steps",
+                   "l2": "inputs larger than L2 (Lanczos basis 4.2 GB streamed every step)",
+                   "parallelism": f"replicas{world}"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "roofline": roof,
+        "kernels": per_kind,
+        "e2e": {"value": round(world * psteps / e2e_t, 1) if t_e2e is not None else None, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "evc_set_values(V from pinned host) + evc_count_slices (host outputs)"},
+        "fp64": None if ms_fp64 is None else {
+            "value": round(world * psteps / (ms_fp64 / fp64_steps * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(ms_fp64 / fp64_steps, 3)},
+        "estimate": {"mixed": est_mixed, "fp64": est_fp64,
+                     "mixed_minus_fp64": (est_mixed - est_fp64) if est_fp64 is not None else None,
+                     "n_below_mixed": [float(x) for x in L_mixed],
+                     "n_below_fp64": None if L_fp64 is None else [float(x) for x in L_fp64]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W, args.cpu_probes, seed=args.seed)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(W, nprobe_sample, seed=0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    if W.kind == "stencil":
+        V = W.potential()
+        pk = {"identity": O.PREC_NONE, "jacobi": O.PREC_JACOBI, "cheb": O.PREC_CHEB}[W.precond]
+        P = O.Problem.stencil(W.N, W.h, W.order, V, pk, cheb_degree=int(W.prec_params[0]),
+                              cheb_c=float(W.prec_params[1]), jac_eps=float(W.prec_params[0]))
+    else:
+        pk = {"identity": O.PREC_NONE, "jacobi": O.PREC_JACOBI}[W.precond]
+        P = O.Problem.csr_matrix(W.csr(), pk, jac_eps=float(W.prec_params[0]))
+    t0 = time.perf_counter()
+    q, st, L = O.count(P, W.shifts, nprobe_sample, W.maxsteps, tol=W.tol, seed=seed,
+                       nthreads=cores)
+    dt = time.perf_counter() - t0
+    ps = float(len(W.shifts) * nprobe_sample * W.maxsteps)
+    return {"value": round(ps / dt, 2), "unit": UNIT, "cores": min(cores, len(W.shifts) * nprobe_sample),
+            "kind": "oracle",
+            "sample": f"{len(W.shifts)} shifts x {nprobe_sample} probes x {W.maxsteps} steps at full n",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1602_02306_gb300 import workloads
+    W = workloads.WORKLOADS[args.workload]()
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    times, vals = [], []
+    for _ in range(args.steps):
+        cb = cpu_baseline(W, args.cpu_probes, seed=args.seed)
+        times.append(cb["seconds"])
+        vals.append(cb["value"])
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1000 * float(np.median(times)), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": W.name, "n": W.n},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "kind": "oracle",
+                             "cores": min(os.cpu_count() or 1, len(W.shifts) * args.cpu_probes),
+                             "sample": f"{len(W.shifts)} shifts x {args.cpu_probes} probes x "
+                                       f"{W.maxsteps} steps at full n per step"},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fd64")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-probes", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison leg")
+    ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

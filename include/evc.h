@@ -1,0 +1,225 @@
+/*
+ * evc.h -- C ABI of libevc, a GB300 (sm_103a) implementation of the
+ * preconditioned Lanczos eigenvalue-count estimator of Vecharynski & Yang,
+ * "Preconditioned iterative methods for eigenvalue counts".
+ *
+ * What it computes (Sec. 2 and Sec. 3 of the paper):
+ *   For a real symmetric A and a shift tau, n_-(A - tau I) = trace h(C) with
+ *   C = M (A - tau I) M, T = M^2 an SPD preconditioner and h the step
+ *   function of Eq. (h) (h(x) = 1 for x < 0, else 0).  For each of m seeded
+ *   Rademacher probes v_j, k steps of Lanczos with full reorthogonalisation
+ *   (Algorithm 1) give a tridiagonal J_k; Gauss quadrature (Eq. gauss_quad)
+ *   gives v_j^T h(C) v_j ~ ||v_j||^2 sum_{theta_i < 0} z_i(1)^2 and the
+ *   estimator L_tau(k, m) (Eq. rand_prec_quad, Algorithm 2) is their mean.
+ *   The count in [xi, eta] is L_eta - L_xi (Sec. 3, two runs of Algorithm 2).
+ *
+ * Conventions
+ *   - Every function returns an evc_status (0 = EVC_OK) and never aborts.
+ *     evc_last_error(ctx) describes the last failure on that context.
+ *   - Output arrays are caller-allocated HOST memory unless stated.
+ *   - A context owns one CUDA stream binding (the caller's stream, or the
+ *     legacy default stream when NULL); calls on one context must not run
+ *     concurrently from several host threads.
+ *   - Probes: v_j[i] = -1 if bit 63 of x is set, else +1, where
+ *     x = mix(seed ^ mix((j << 32) | i)) and mix is the SplitMix64 output
+ *     finaliser.  The same probes serve every shift of one call.
+ *   - Real symmetric matrices only.
+ */
+#ifndef EVC_H
+#define EVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evc_ctx evc_ctx;
+
+typedef enum {
+    EVC_OK = 0,
+    EVC_EINVAL = 1,        /* invalid argument (message in evc_last_error)      */
+    EVC_ENOMEM = 2,        /* device or host allocation failed / workspace small */
+    EVC_ECUDA = 3,         /* a CUDA runtime call failed                         */
+    EVC_ENUMERIC = 4,      /* NaN/Inf in alpha/beta or eigensolver did not converge */
+    EVC_ETIMEOUT = 5,      /* a bounded device wait gave up                      */
+    EVC_EUNSUPPORTED = 6   /* valid request this build does not implement        */
+} evc_status;
+
+/* Arithmetic of the path.
+ *   EVC_FP64 : matrix values, vectors and all arithmetic in float64.
+ *   EVC_MIXED: matrix values, probe blocks, Lanczos basis, operator and
+ *              preconditioner applies in float32; alpha, beta, the
+ *              reorthogonalisation coefficients, the tridiagonal eigensolve
+ *              and the quadrature weights in float64 (dot products accumulate
+ *              short float32 runs and sum them in float64).                 */
+enum { EVC_FP64 = 0, EVC_MIXED = 1 };
+
+/* Preconditioners T = M^2 (Sec. 6; all SPD, so C keeps the inertia of
+ * A - tau I, Sec. 2 Eq. negi_T).
+ *   EVC_PREC_IDENTITY    : M = I.
+ *   EVC_PREC_JACOBI      : M = diag((|a_ii - tau| + eps)^(-1/2)), per shift;
+ *                          param0 = eps (> 0, default 1e-3).
+ *   EVC_PREC_CHEB_KINETIC: stencil contexts only.  M = p_d(K), K = -1/2 Lap_h
+ *                          + c I with the context's stencil, p_d the degree-d
+ *                          Chebyshev interpolant (first-kind nodes) of
+ *                          x^(-1/2) on the closed-form spectral interval
+ *                          [c, c + 6/h^2] (7-point) or [c, c + 8/h^2]
+ *                          (13-point) of K; shift independent (Sec. 3: one
+ *                          T may serve both runs).  param0 = d (1..32),
+ *                          param1 = c (> 0).  Fails with EVC_EINVAL when p_d
+ *                          is not positive on the discrete spectrum of K.  */
+enum { EVC_PREC_IDENTITY = 0, EVC_PREC_JACOBI = 1, EVC_PREC_CHEB_KINETIC = 2 };
+
+/* Largest number of Lanczos steps per call. */
+#define EVC_MAX_STEPS 256
+
+/* A CSR matrix (Sec. 1: A large, sparse, symmetric).
+ *   n, nnz      : order and stored entries (0 < n < 2^31, nnz < 2^62).
+ *   row_ptr     : int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *   col         : int32[nnz], 0 <= col < n (duplicates are summed).
+ *   val         : float64[nnz], or float32[nnz] when val_is_fp32 = 1.
+ *   on_device   : 0 = host pointers (the library copies them into device
+ *                 memory it owns); 1 = device pointers, borrowed (they must
+ *                 stay valid until evc_destroy) when val's type matches the
+ *                 context precision, else copied/converted.
+ *   check       : 1 = validate ranges and symmetry on the host (host input
+ *                 only); 0 = trust the caller.                                */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+    int32_t val_is_fp32;
+    int32_t on_device;
+    int32_t check;
+    int32_t reserved;
+} evc_csr;
+
+/* Create a context for a CSR matrix.  precision: EVC_FP64 or EVC_MIXED.
+ * stream: a cudaStream_t (NULL = legacy default stream).  *out receives the
+ * context; on failure *out is NULL.                                          */
+int evc_create_csr(const evc_csr* A, int precision, void* stream, evc_ctx** out);
+
+/* Create a context for the periodic finite-difference Hamiltonian
+ * H = -1/2 Lap_h + diag(V) on an N^3 grid with spacing h (the real-space DFT
+ * setting of Sec. 7).  order 2 = 7-point, order 4 = 13-point Laplacian.
+ * V: N^3 values, point p = x + N*(y + N*z), float64 (or float32 when
+ * V_is_fp32 = 1), host (copied) or device (on_device = 1: borrowed if its
+ * type matches the precision, else converted).  N >= 2 (order 2), N >= 5
+ * (order 4), N^3 < 2^31.                                                     */
+int evc_create_stencil(int N, double h, int order, const void* V, int V_is_fp32,
+                       int on_device, int precision, void* stream, evc_ctx** out);
+
+/* Replace the matrix values without changing the structure: V (stencil
+ * context, N^3 values) or the CSR values (nnz values), with the type given
+ * at creation.  Host (on_device = 0) or device pointer; copied into the
+ * context's own device buffer on its stream.                                  */
+int evc_set_values(evc_ctx* ctx, const void* values, int on_device);
+
+/* Choose the preconditioner (see the EVC_PREC_* list above).                */
+int evc_set_precond(evc_ctx* ctx, int kind, double param0, double param1);
+
+/* Device scratch needed by a call with nshift shifts, nprobe probes and
+ * maxsteps steps (bytes).  The Lanczos basis dominates:
+ * (maxsteps + 1) * n * ceil(nshift*nprobe/32)*32 * (8 or 4) bytes.           */
+size_t evc_workspace_bytes(const evc_ctx* ctx, int nshift, int nprobe, int maxsteps);
+
+/* Hand the context caller-owned device scratch (for instance from a PyTorch
+ * allocator).  The memory must stay valid until it is replaced or the
+ * context is destroyed; bytes >= evc_workspace_bytes(...) of the calls that
+ * follow, else they fail with EVC_ENOMEM.  dptr = NULL returns to scratch
+ * the library allocates itself (cudaMalloc, grown on demand).                 */
+int evc_set_workspace(evc_ctx* ctx, void* dptr, size_t bytes);
+
+/* Algorithm 2 twice (Sec. 3): estimate of the number of eigenvalues of A in
+ * [xi, eta] (xi < eta).
+ *   nprobe      : m >= 1 probes (ids 0..m-1), the same for both shifts.
+ *   maxsteps    : k, 1..EVC_MAX_STEPS, clamped to n.
+ *   tol         : <= 0 runs exactly k steps; > 0 stops a shift after the
+ *                 first step i >= 2 with |L(i) - L(i-1)| <= tol.
+ *   estimate    : L_eta - L_xi (real; the paper's count is its rounding).
+ *   per_probe_quad (may be NULL): double[2*nprobe], [0..m) for xi, [m..2m) eta.
+ *   steps_used  (may be NULL): int[2].
+ * Blocks until the results are on the host.                                   */
+int evc_count(evc_ctx* ctx, double xi, double eta, int nprobe, int maxsteps,
+              double tol, uint64_t seed, double* estimate, double* per_probe_quad,
+              int* steps_used);
+
+/* Algorithm 2 for nshift shifts in one batched launch (spectrum slicing,
+ * Sec. 1): n_below[s] = L_{shifts[s]}(k, m), the estimate of
+ * n_-(A - shifts[s] I).  Slice counts are differences of consecutive
+ * entries.  per_probe_quad: double[nshift*nprobe] (may be NULL),
+ * steps_used: int[nshift] (may be NULL).                                      */
+int evc_count_slices(evc_ctx* ctx, const double* shifts, int nshift, int nprobe,
+                     int maxsteps, double tol, uint64_t seed, double* n_below,
+                     double* per_probe_quad, int* steps_used);
+
+/* Same as evc_count_slices, but leaves the results on the device: d_quad
+ * (double[nshift*nprobe]), d_n_below (double[nshift]) and d_steps
+ * (int32[nshift]) are device pointers (any may be NULL).  Enqueues the work
+ * on the context's stream and returns without waiting; errors raised on the
+ * device are reported by the next synchronising call.                         */
+int evc_count_slices_async(evc_ctx* ctx, const double* shifts, int nshift, int nprobe,
+                           int maxsteps, double tol, uint64_t seed, double* d_n_below,
+                           double* d_quad, int* d_steps);
+
+/* Wait for the context's stream and report any error raised on the device by
+ * the work enqueued so far.                                                   */
+int evc_sync(evc_ctx* ctx);
+
+/* The tridiagonal matrices of the last call (Sec. 3, Eq. Tk), for
+ * diagnostics: alpha[c*maxsteps + i] = alpha_{i+1}, beta[c*(maxsteps+1) + i]
+ * = beta_{i+1} (beta_1 = 0) of column c = s*nprobe + j; kdone[c] = steps the
+ * column completed (< maxsteps after a Lanczos breakdown).  Host arrays of
+ * the sizes implied by the last call's nshift, nprobe and maxsteps.          */
+int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
+
+/* Options.
+ *   EVC_OPT_GRAPH  : 1 (default) replays the whole multi-step launch sequence
+ *                    as one CUDA graph, 0 launches kernels one by one.
+ *   EVC_OPT_PROFILE: 1 brackets every kernel launch with a pair of timing
+ *                    events on the context's stream (inside the graph when
+ *                    graphs are on); 0 (default) records nothing.           */
+enum { EVC_OPT_GRAPH = 1, EVC_OPT_PROFILE = 2 };
+int evc_set_option(evc_ctx* ctx, int option, int64_t value);
+
+/* Kernel classes reported by evc_get_profile.                               */
+enum {
+    EVC_K_INIT = 0,      /* probe generation and state reset                  */
+    EVC_K_JACOBI = 1,    /* Jacobi scales per shift                           */
+    EVC_K_STENCIL = 2,   /* one stencil pass (Chebyshev step / H apply)       */
+    EVC_K_CSR = 3,       /* CSR operator apply                                */
+    EVC_K_DOTS = 4,      /* reorthogonalisation dot products                  */
+    EVC_K_REDUCE = 5,    /* dot-product reduction, alpha                      */
+    EVC_K_UPDATE = 6,    /* reorthogonalisation update and norm               */
+    EVC_K_FINISH = 7     /* beta, eigensolve, quadrature, stop rule           */
+};
+
+/* One kernel launch of the last call: its class, Lanczos step (0 = set-up),
+ * device time in milliseconds (events on the context's stream; -1 when
+ * profiling was off) and the compulsory HBM bytes of the launch (every
+ * operand read once, every output written once, all chunks active).          */
+typedef struct {
+    int32_t kind;
+    int32_t step;
+    double ms;
+    double bytes;
+} evc_prof_rec;
+
+/* Launch list of the last call.  Writes min(cap, launches) records to recs
+ * (may be NULL) and the number of kernel launches of one call to *nrec.
+ * Synchronises the context's stream.                                          */
+int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
+
+const char* evc_last_error(const evc_ctx* ctx);
+void evc_destroy(evc_ctx* ctx);
+/* Library version, major*10000 + minor*100 + patch.                           */
+int evc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVC_H */

@@ -1,0 +1,1093 @@
+// evc_api.cu -- host side of libevc: the C ABI of include/evc.h.
+//
+// A call of evc_count_slices runs Algorithm 2 of the paper for S shifts and
+// m probes at once: the S*m (shift, probe) columns are packed into 32-wide
+// chunks, and every Lanczos step (Algorithm 1) is a fixed sequence of kernel
+// launches over all active chunks:
+//   operator passes  w = M (A - sigma I) M q_i - beta_i q_{i-1}
+//   reorth           h = Q_i^T w, alpha_i = h_i, w -= Q_i h, ||w||^2
+//   finish           beta_{i+1}, breakdown, eig(J_i) -> quadrature, stop rule
+// The whole k-step sequence is captured once into a CUDA graph and replayed;
+// the per-call values (shifts, seed, tol) live in device memory so a replay
+// needs only a few small copies.  Shifts that meet the stop rule switch their
+// chunks off on the device and the kernels skip them.
+#include "evc_internal.cuh"
+#include "../../include/evc.h"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace evc;
+
+namespace {
+
+enum { OP_CSR = 0, OP_STENCIL = 1 };
+
+struct GraphKey {
+    int S = -1, m = -1, kmax = -1, adaptive = -1, prec_version = -1, profile = -1;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool operator==(const GraphKey& o) const
+    {
+        return S == o.S && m == o.m && kmax == o.kmax && adaptive == o.adaptive &&
+               prec_version == o.prec_version && profile == o.profile && ws == o.ws &&
+               ws_bytes == o.ws_bytes;
+    }
+};
+
+}  // namespace
+
+struct evc_ctx {
+    int op = OP_CSR;
+    int precision = EVC_FP64;
+    size_t tsize = 8;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t n = 0;
+    // CSR
+    CsrOp csr{};
+    int64_t nnz = 0;
+    void* own_rowptr = nullptr;
+    void* own_col = nullptr;
+    void* own_val = nullptr;
+    double* own_diag = nullptr;
+    // stencil
+    StencilOp sten{};
+    void* own_V = nullptr;
+    // preconditioner
+    int prec = EVC_PREC_IDENTITY;
+    double jac_eps = 1e-3;
+    int cheb_degree = 0;
+    double cheb_c = 1.0;
+    double cheb_a = 0, cheb_b = 0;
+    std::vector<double> cheb_coef;
+    int prec_version = 0;
+    // workspace
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    // pinned staging: per-call parameters (guarded by an event) and results
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+    void* pinres = nullptr;
+    size_t pinres_bytes = 0;
+    cudaEvent_t param_ev = nullptr;
+    // launch list of the enqueued sequence (with timing events when profiling)
+    bool profile = false;
+    struct Rec { int kind, step; double bytes; cudaEvent_t e0, e1; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
+    // graph
+    bool use_graph = true;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    // last run
+    Run run{};
+    bool have_run = false;
+    std::string err;
+};
+
+namespace {
+
+int fail(evc_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(evc_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, EVC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int choose_nblk(int64_t n, int nchunk)
+{
+    // about 4 resident blocks per SM on 152 SMs; at least 64 rows per block
+    const int64_t target = (4 * 152 + nchunk - 1) / nchunk;
+    const int64_t maxb = std::max<int64_t>(1, (n + 63) / 64);
+    return (int)std::max<int64_t>(1, std::min(target, maxb));
+}
+
+struct Layout {
+    size_t total;
+    int nchunk, ncol, nblk;
+};
+
+bool uses_work(const evc_ctx* c) { return c->op == OP_STENCIL && c->prec == EVC_PREC_CHEB_KINETIC; }
+bool uses_jac(const evc_ctx* c) { return c->prec == EVC_PREC_JACOBI; }
+
+// Carve the workspace into the run's arrays with one cursor, so the size
+// query (base = 0) and the real carving can never disagree.  Every array
+// starts on a 256-byte boundary.
+size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void** work)
+{
+    const int ncol_real = S * m;
+    const int nchunk = (ncol_real + CW - 1) / CW;
+    const int ncol = nchunk * CW;
+    const int nblk = choose_nblk(c->n, nchunk);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    const size_t vec = (size_t)c->n * CW * c->tsize;
+    r.n = c->n;
+    r.S = S;
+    r.m = m;
+    r.kmax = kmax;
+    r.ncol = ncol;
+    r.ncol_real = ncol_real;
+    r.nchunk = nchunk;
+    r.nblk = nblk;
+    r.slot_stride = c->n * CW;
+    r.chunk_stride = (int64_t)(kmax + 1) * c->n * CW;
+    r.basis = take((size_t)nchunk * (kmax + 1) * vec);
+    void* w = uses_work(c) ? take(3 * (size_t)nchunk * vec) : nullptr;
+    if (work) *work = w;
+    r.jac = uses_jac(c) ? take((size_t)S * c->n * c->tsize) : nullptr;
+    auto D = [&](size_t cnt) { return reinterpret_cast<double*>(take(cnt * 8)); };
+    auto I = [&](size_t cnt) { return reinterpret_cast<int*>(take(cnt * 4)); };
+    r.sigma = D(ncol);
+    r.alpha = D((size_t)kmax * ncol);
+    r.beta = D((size_t)(kmax + 1) * ncol);
+    r.scl = D((size_t)(kmax + 1) * ncol);
+    r.g = D((size_t)kmax * ncol);
+    r.ppc = D(ncol);
+    r.colscale = D(ncol);
+    r.quad = D(ncol);
+    r.quad_final = D(ncol);
+    r.probe_id = reinterpret_cast<int64_t*>(take((size_t)ncol * 8));
+    r.shift_of = I(ncol);
+    r.kdone = I(ncol);
+    r.shifts = D(S);
+    r.Lprev = D(S);
+    r.Lfinal = D(S);
+    r.steps = I(S);
+    r.sdone = I(S);
+    r.chunk_active = I(nchunk);
+    r.part_dot = D((size_t)nchunk * nblk * kmax * CW);
+    r.part_nrm = D((size_t)nchunk * nblk * CW);
+    r.eigw = D((size_t)3 * kmax * ncol);
+    r.err = I(1);
+    r.seed = reinterpret_cast<uint64_t*>(take(8));
+    r.tol = D(1);
+    r.breakdown_rel = c->precision == EVC_FP64 ? 1e-12 : 1e-6;
+    return off;
+}
+
+Layout layout(const evc_ctx* c, int S, int m, int kmax)
+{
+    Run r{};
+    Layout L;
+    L.total = carve(c, S, m, kmax, nullptr, r, nullptr);
+    L.nchunk = r.nchunk;
+    L.ncol = r.ncol;
+    L.nblk = r.nblk;
+    return L;
+}
+
+// ------------------------------------------------------------ conversions
+
+template <typename D, typename S_>
+__global__ void convert_kernel(D* dst, const S_* src, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (D)src[i];
+}
+
+__global__ void csr_diag_kernel(const int64_t* rp, const int32_t* col, const void* val, int fp32,
+                                double* diag, int64_t n)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int64_t k = rp[r]; k < rp[r + 1]; ++k)
+            if (col[k] == r)
+                d += fp32 ? (double)static_cast<const float*>(val)[k]
+                          : static_cast<const double*>(val)[k];
+        diag[r] = d;
+    }
+}
+
+int upload_values(evc_ctx* ctx, void* dst, const void* src, int64_t count, int src_fp32,
+                  int on_device)
+{
+    const size_t ssz = src_fp32 ? 4 : 8;
+    const bool same = (src_fp32 ? 4u : 8u) == ctx->tsize;
+    if (same) {
+        CU(cudaMemcpyAsync(dst, src, count * ssz, on_device ? cudaMemcpyDeviceToDevice
+                                                            : cudaMemcpyHostToDevice,
+                           ctx->stream));
+        return EVC_OK;
+    }
+    const void* dsrc = src;
+    void* tmp = nullptr;
+    if (!on_device) {
+        CU(cudaMalloc(&tmp, count * ssz));
+        CU(cudaMemcpyAsync(tmp, src, count * ssz, cudaMemcpyHostToDevice, ctx->stream));
+        dsrc = tmp;
+    }
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
+    if (ctx->tsize == 4)
+        convert_kernel<float, double><<<blocks, 256, 0, ctx->stream>>>(
+            static_cast<float*>(dst), static_cast<const double*>(dsrc), count);
+    else
+        convert_kernel<double, float><<<blocks, 256, 0, ctx->stream>>>(
+            static_cast<double*>(dst), static_cast<const float*>(dsrc), count);
+    CU(cudaGetLastError());
+    if (tmp) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaFree(tmp));
+    }
+    return EVC_OK;
+}
+
+// ---------------------------------------------------------- Chebyshev M
+
+// Symbol of -1/2 d^2/dx^2 (one axis) at wavenumber theta.
+double axis_symbol(int order, double h, double th)
+{
+    if (order == 2) return (1.0 - std::cos(th)) / (h * h);
+    return (30.0 - 32.0 * std::cos(th) + 2.0 * std::cos(2.0 * th)) / (24.0 * h * h);
+}
+
+double cheb_eval(const std::vector<double>& c, double a, double b, double x)
+{
+    // Clenshaw summation of sum_j c_j T_j(t), t = (2x - a - b)/(b - a)
+    const double t = (2.0 * x - a - b) / (b - a);
+    double b1 = 0.0, b2 = 0.0;
+    for (int j = (int)c.size() - 1; j >= 1; --j) {
+        const double b0 = c[j] + 2.0 * t * b1 - b2;
+        b2 = b1;
+        b1 = b0;
+    }
+    return c[0] + t * b1 - b2;
+}
+
+}  // namespace
+
+int evc::cheb_coefficients(int degree, double a, double b, double* coef)
+{
+    // Interpolation of f(x) = x^(-1/2) at the d+1 Chebyshev points of the first
+    // kind mapped to [a, b]: c_j = (2/(d+1)) sum_k f(x_k) T_j(t_k), c_0 halved.
+    const int np = degree + 1;
+    const double pi = 3.141592653589793238462643;
+    std::vector<double> f(np);
+    for (int k = 0; k < np; ++k) {
+        const double th = pi * (2 * k + 1) / (2.0 * np);
+        f[k] = 1.0 / std::sqrt(0.5 * (a + b) + 0.5 * (b - a) * std::cos(th));
+    }
+    for (int j = 0; j <= degree; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < np; ++k) s += f[k] * std::cos(j * pi * (2 * k + 1) / (2.0 * np));
+        coef[j] = (j == 0 ? 1.0 : 2.0) * s / np;
+    }
+    return 0;
+}
+
+namespace {
+
+// ------------------------------------------------------- step sequence
+
+cudaEvent_t pool_event(evc_ctx* ctx)
+{
+    if (ctx->evnext == ctx->evpool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->evpool.push_back(e);
+    }
+    return ctx->evpool[ctx->evnext++];
+}
+
+// Enqueue one kernel launch, bracketed by timing events when profiling.
+template <class F>
+int rec(evc_ctx* ctx, int kind, int step, double bytes, F&& launch)
+{
+    evc_ctx::Rec r{kind, step, bytes, nullptr, nullptr};
+    if (ctx->profile) {
+        r.e0 = pool_event(ctx);
+        r.e1 = pool_event(ctx);
+        if (!r.e0 || !r.e1) return fail(ctx, EVC_ECUDA, "cudaEventCreate failed");
+        // external record nodes when captured, so the events can be timed after a replay
+        CU(cudaEventRecordWithFlags(r.e0, ctx->stream, cudaEventRecordExternal));
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess)
+        return fail(ctx, EVC_ECUDA, "kernel launch (class %d, step %d): %s", kind, step,
+                    cudaGetErrorString(e));
+    if (ctx->profile) CU(cudaEventRecordWithFlags(r.e1, ctx->stream, cudaEventRecordExternal));
+    ctx->recs.push_back(r);
+    return EVC_OK;
+}
+
+enum BKind { B_ZERO, B_XMUL, B_BUF };
+struct BTerm {
+    BKind kind = B_ZERO;
+    double gamma = 0.0;
+    void* buf = nullptr;
+};
+
+template <typename T>
+double stencil_bytes(const evc_ctx* ctx, const Run& r, const StencilPass& p, bool jac)
+{
+    const double vec = (double)r.nchunk * r.n * CW * sizeof(T);
+    double b = vec * (2 + (p.x ? 1 : 0) + (p.prev ? 1 : 0) + (p.pp ? 1 : 0));
+    if (p.useV) b += (double)r.n * sizeof(T);
+    if (jac) b += (double)r.S * r.n * sizeof(T);
+    return b;
+}
+
+template <typename T>
+int stencil(evc_ctx* ctx, const Run& r, int step, const StencilPass& p, bool jac)
+{
+    return rec(ctx, EVC_K_STENCIL, step, stencil_bytes<T>(ctx, r, p, jac),
+               [&] { return launch_stencil_pass<T>(ctx->sten, r, p, jac, ctx->stream); });
+}
+
+// y = p_d(K) x by Clenshaw's recurrence b_j = c_j x + 2 K~ b_{j+1} - b_{j+2},
+// y = c_0 x + K~ b_1 - b_2, K~ = (2K - (a+b)I)/(b-a).  Terms that are still
+// multiples of x are folded into the next pass, so degree d costs d passes;
+// b_j overwrites b_{j+2} in place (it is read only at its own point).
+template <typename T>
+int enqueue_cheb(evc_ctx* ctx, const Run& r, int step, const void* x, int64_t x_cs,
+                 const double* xscale, void* W0, void* W1, void* out, int64_t out_cs,
+                 const void* pp, int64_t pp_cs, const double* ppc)
+{
+    const int d = ctx->cheb_degree;
+    const std::vector<double>& c = ctx->cheb_coef;
+    const double a = ctx->cheb_a, b = ctx->cheb_b;
+    const double kap1 = 2.0 / (b - a), kap0 = (2.0 * ctx->cheb_c - a - b) / (b - a);
+    const int64_t wcs = r.n * CW;
+    BTerm b1, b2;   // b_{j+1}, b_{j+2}
+    for (int j = d; j >= 0; --j) {
+        const bool final_ = (j == 0);
+        const double f = final_ ? 1.0 : 2.0;
+        if (!final_ && b1.kind == B_ZERO && b2.kind == B_ZERO) {
+            b1.kind = B_XMUL;
+            b1.gamma = c[j];
+            continue;
+        }
+        StencilPass p{};
+        if (b1.kind == B_XMUL) {
+            p.in = x;
+            p.in_cs = x_cs;
+            p.insc = xscale;
+            p.k1 = f * b1.gamma * kap1;
+            p.k0 = f * b1.gamma * kap0 + c[j];
+            if (b2.kind == B_XMUL) p.k0 -= b2.gamma;
+        } else {
+            p.in = b1.buf;
+            p.in_cs = wcs;
+            p.k1 = f * kap1;
+            p.k0 = f * kap0;
+            p.x = x;
+            p.x_cs = x_cs;
+            p.xs = xscale;
+            p.a0 = c[j];
+            if (b2.kind == B_XMUL) p.a0 -= b2.gamma;
+            if (b2.kind == B_BUF) {
+                p.prev = b2.buf;
+                p.prev_cs = wcs;
+                p.a2 = 1.0;
+            }
+        }
+        void* dst;
+        int64_t dst_cs = wcs;
+        if (final_) {
+            dst = out;
+            dst_cs = out_cs;
+            p.pp = pp;
+            p.pp_cs = pp_cs;
+            p.ppc = pp ? ppc : nullptr;
+        } else if (b2.kind == B_BUF) {
+            dst = b2.buf;
+        } else {
+            dst = (b1.kind == B_BUF && b1.buf == W0) ? W1 : W0;
+        }
+        p.out = dst;
+        p.out_cs = dst_cs;
+        int rc = stencil<T>(ctx, r, step, p, false);
+        if (rc) return rc;
+        if (final_) break;
+        BTerm nb;
+        nb.kind = B_BUF;
+        nb.buf = dst;
+        b2 = b1;
+        b1 = nb;
+    }
+    return EVC_OK;
+}
+
+template <typename T>
+int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
+{
+    cudaStream_t st = ctx->stream;
+    const double vec = (double)r.nchunk * r.n * CW * sizeof(T);
+    const double colb = (double)r.ncol * 8;
+    int rc = rec(ctx, EVC_K_INIT, 0, colb * 8, [&] { return launch_init_state(r, st); });
+    if (!rc) rc = rec(ctx, EVC_K_INIT, 0, vec, [&] { return launch_init_probe<T>(r, st); });
+    if (!rc && uses_jac(ctx)) {
+        const double vdiag = ctx->op == OP_STENCIL ? ctx->sten.cd : 0.0;
+        rc = rec(ctx, EVC_K_JACOBI, 0, (double)r.S * r.n * sizeof(T) + r.n * 8.0, [&] {
+            return launch_jacobi_scales<T>(r, ctx->op == OP_CSR ? ctx->csr.diag : nullptr,
+                                           ctx->op == OP_STENCIL ? ctx->sten.V : nullptr, vdiag,
+                                           ctx->jac_eps, st);
+        });
+    }
+    if (rc) return rc;
+    T* basis = static_cast<T*>(r.basis);
+    const int64_t vstride = r.n * CW;
+    for (int i = 1; i <= r.kmax && !rc; ++i) {
+        T* qi = basis + (int64_t)(i - 1) * r.slot_stride;
+        T* qprev = i >= 2 ? basis + (int64_t)(i - 2) * r.slot_stride : nullptr;
+        T* wout = basis + (int64_t)i * r.slot_stride;
+        const double* si = r.scl + (int64_t)(i - 1) * r.ncol;
+        if (ctx->op == OP_CSR) {
+            const double ab = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1);
+            const double b = ab + vec * (2 + (qprev ? 1 : 0)) +
+                             (uses_jac(ctx) ? (double)r.S * r.n * sizeof(T) : 0.0);
+            rc = rec(ctx, EVC_K_CSR, i, b,
+                     [&] { return launch_csr_pass<T>(ctx->csr, r, i, uses_jac(ctx), st); });
+        } else if (ctx->prec == EVC_PREC_CHEB_KINETIC) {
+            T* W0 = static_cast<T*>(work);
+            T* W1 = W0 + (int64_t)r.nchunk * vstride;
+            T* W2 = W1 + (int64_t)r.nchunk * vstride;
+            // u = M q_i into W2
+            rc = enqueue_cheb<T>(ctx, r, i, qi, r.chunk_stride, si, W0, W1, W2, vstride, nullptr,
+                                 0, nullptr);
+            if (rc) return rc;
+            // t = (H - sigma I) u into W0
+            StencilPass p{};
+            p.in = W2;
+            p.in_cs = vstride;
+            p.k1 = 1.0;
+            p.useV = 1;
+            p.useSigma = 1;
+            p.out = W0;
+            p.out_cs = vstride;
+            rc = stencil<T>(ctx, r, i, p, false);
+            if (rc) return rc;
+            // w = M t - beta_i q_{i-1} into slot i
+            rc = enqueue_cheb<T>(ctx, r, i, W0, vstride, nullptr, W1, W2, wout, r.chunk_stride,
+                                 qprev, r.chunk_stride, r.ppc);
+        } else {
+            StencilPass p{};
+            p.in = qi;
+            p.in_cs = r.chunk_stride;
+            p.insc = si;
+            p.k1 = 1.0;
+            p.useV = 1;
+            p.useSigma = 1;
+            p.out = wout;
+            p.out_cs = r.chunk_stride;
+            p.pp = qprev;
+            p.pp_cs = r.chunk_stride;
+            p.ppc = qprev ? r.ppc : nullptr;
+            rc = stencil<T>(ctx, r, i, p, uses_jac(ctx));
+        }
+        if (rc) return rc;
+        rc = rec(ctx, EVC_K_DOTS, i, vec * (i + 1), [&] { return launch_dots<T>(r, i, st); });
+        if (!rc)
+            rc = rec(ctx, EVC_K_REDUCE, i, (double)r.nchunk * r.nblk * i * CW * 8 + colb * 2 * i,
+                     [&] { return launch_reduce(r, i, st); });
+        if (!rc)
+            rc = rec(ctx, EVC_K_UPDATE, i, vec * (i + 2), [&] { return launch_update<T>(r, i, st); });
+        const bool last = (i == r.kmax);
+        if (!rc)
+            rc = rec(ctx, EVC_K_FINISH, i, (double)r.nchunk * r.nblk * CW * 8 + colb * 8,
+                     [&] { return launch_finish(r, i, adaptive || last, last, st); });
+        if (!rc) rc = rec(ctx, EVC_K_FINISH, i, colb, [&] { return launch_active(r, st); });
+    }
+    return rc;
+}
+
+int ensure_pinned(evc_ctx* ctx, void** buf, size_t* have, size_t bytes)
+{
+    if (*have >= bytes) return EVC_OK;
+    if (*buf) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        cudaFreeHost(*buf);
+    }
+    *buf = nullptr;
+    *have = 0;
+    CU(cudaHostAlloc(buf, bytes, cudaHostAllocDefault));
+    *have = bytes;
+    return EVC_OK;
+}
+
+void drop_graph(evc_ctx* ctx)
+{
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gkey = GraphKey();
+}
+
+// Validate, size the workspace, upload the per-call parameters and enqueue
+// (or replay) the run.  Results stay on the device.
+int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, double tol,
+              uint64_t seed)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (!shifts || S < 1) return fail(ctx, EVC_EINVAL, "need at least one shift");
+    if (m < 1) return fail(ctx, EVC_EINVAL, "nprobe must be >= 1 (got %d)", m);
+    if (maxsteps < 1 || maxsteps > EVC_MAX_STEPS)
+        return fail(ctx, EVC_EINVAL, "maxsteps must be in [1, %d] (got %d)", EVC_MAX_STEPS, maxsteps);
+    if ((int64_t)S * m > (int64_t)1 << 26) return fail(ctx, EVC_EINVAL, "too many columns");
+    if ((uint64_t)m + CW > ((uint64_t)1 << 32)) return fail(ctx, EVC_EINVAL, "nprobe too large");
+    if (((int64_t)S * m + CW - 1) / CW > 65535)
+        return fail(ctx, EVC_EINVAL, "at most 65535*32 (shift, probe) columns per call");
+    for (int s = 0; s < S; ++s)
+        if (!std::isfinite(shifts[s])) return fail(ctx, EVC_EINVAL, "shift %d is not finite", s);
+    if (!std::isfinite(tol)) return fail(ctx, EVC_EINVAL, "tol is not finite");
+    const int kmax = (int)std::min<int64_t>(maxsteps, ctx->n);
+    Layout L = layout(ctx, S, m, kmax);
+    if (L.total > ctx->ws_bytes) {
+        if (!ctx->ws_owned && ctx->ws)
+            return fail(ctx, EVC_ENOMEM, "workspace too small: need %zu bytes, have %zu", L.total,
+                        ctx->ws_bytes);
+        drop_graph(ctx);
+        if (ctx->ws) cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->ws, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, EVC_ENOMEM, "cudaMalloc of %zu bytes failed: %s", L.total,
+                        cudaGetErrorString(e));
+        }
+        ctx->ws_bytes = L.total;
+        ctx->ws_owned = true;
+    }
+    Run r{};
+    void* work = nullptr;
+    carve(ctx, S, m, kmax, static_cast<char*>(ctx->ws), r, &work);
+
+    // per-call parameters: sigma / shift_of / probe_id per column, shifts, seed, tol
+    const size_t pbytes = (size_t)L.ncol * (8 + 8 + 4) + (size_t)S * 8 + 64;
+    // the previous call's parameter copies must have left the staging buffer
+    if (ctx->param_ev) CU(cudaEventSynchronize(ctx->param_ev));
+    int rc = ensure_pinned(ctx, &ctx->pinned, &ctx->pinned_bytes, pbytes);
+    if (rc) return rc;
+    char* h = static_cast<char*>(ctx->pinned);
+    double* hsig = reinterpret_cast<double*>(h);
+    int64_t* hpid = reinterpret_cast<int64_t*>(h + (size_t)L.ncol * 8);
+    int* hsh = reinterpret_cast<int*>(h + (size_t)L.ncol * 16);
+    double* hshifts = reinterpret_cast<double*>(h + (size_t)L.ncol * 20);
+    uint64_t* hseed = reinterpret_cast<uint64_t*>(h + (size_t)L.ncol * 20 + (size_t)S * 8);
+    double* htol = reinterpret_cast<double*>(hseed + 1);
+    for (int c = 0; c < L.ncol; ++c) {
+        const bool real = c < S * m;
+        const int s = real ? c / m : S - 1;
+        hsh[c] = s;
+        hsig[c] = shifts[s];
+        hpid[c] = real ? c % m : (int64_t)m + (c - S * m);   // padding: extra probes, ignored
+    }
+    for (int s = 0; s < S; ++s) hshifts[s] = shifts[s];
+    *hseed = seed;
+    *htol = tol;
+    CU(cudaMemcpyAsync(r.sigma, hsig, (size_t)L.ncol * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.probe_id, hpid, (size_t)L.ncol * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.shift_of, hsh, (size_t)L.ncol * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.shifts, hshifts, (size_t)S * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.seed, hseed, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.tol, htol, 8, cudaMemcpyHostToDevice, ctx->stream));
+    if (!ctx->param_ev) CU(cudaEventCreateWithFlags(&ctx->param_ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(ctx->param_ev, ctx->stream));
+
+    const bool adaptive = tol > 0.0;
+    auto enqueue = [&]() -> int {
+        ctx->recs.clear();
+        ctx->evnext = 0;
+        return ctx->tsize == 4 ? enqueue_all<float>(ctx, r, work, adaptive)
+                               : enqueue_all<double>(ctx, r, work, adaptive);
+    };
+    if (ctx->use_graph) {
+        GraphKey k;
+        k.S = S;
+        k.m = m;
+        k.kmax = kmax;
+        k.adaptive = adaptive;
+        k.prec_version = ctx->prec_version;
+        k.profile = ctx->profile;
+        k.ws = ctx->ws;
+        k.ws_bytes = ctx->ws_bytes;
+        if (!(ctx->gexec && k == ctx->gkey)) {
+            drop_graph(ctx);
+            cudaGraph_t g = nullptr;
+            CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue();
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess)
+                return fail(ctx, EVC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ctx->gexec = nullptr;
+                return fail(ctx, EVC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+            }
+            ctx->gkey = k;
+        }
+        CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    } else {
+        rc = enqueue();
+        if (rc) return rc;
+    }
+    ctx->run = r;
+    ctx->have_run = true;
+    return EVC_OK;
+}
+
+int check_device_error(evc_ctx* ctx)
+{
+    int herr = 0;
+    CU(cudaMemcpyAsync(&herr, ctx->run.err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (herr == DERR_NUMERIC)
+        return fail(ctx, EVC_ENUMERIC, "non-finite alpha/beta or tridiagonal eigensolver failure");
+    if (herr) return fail(ctx, EVC_ECUDA, "device error flag %d", herr);
+    return EVC_OK;
+}
+
+int validate_csr_host(evc_ctx* ctx, const evc_csr* A)
+{
+    const int64_t n = A->n, nnz = A->nnz;
+    if (A->row_ptr[0] != 0 || A->row_ptr[n] != nnz)
+        return fail(ctx, EVC_EINVAL, "row_ptr must start at 0 and end at nnz");
+    for (int64_t r = 0; r < n; ++r)
+        if (A->row_ptr[r + 1] < A->row_ptr[r]) return fail(ctx, EVC_EINVAL, "row_ptr decreases at %lld", (long long)r);
+    for (int64_t k = 0; k < nnz; ++k)
+        if (A->col[k] < 0 || A->col[k] >= n) return fail(ctx, EVC_EINVAL, "column index out of range at %lld", (long long)k);
+    // symmetry: sorted (r, c, v) triplets against sorted (c, r, v)
+    struct E { int64_t a, b; double v; };
+    std::vector<E> x((size_t)nnz), y((size_t)nnz);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t k = A->row_ptr[r]; k < A->row_ptr[r + 1]; ++k) {
+            const double v = A->val_is_fp32 ? (double)static_cast<const float*>(A->val)[k]
+                                            : static_cast<const double*>(A->val)[k];
+            if (!std::isfinite(v)) return fail(ctx, EVC_EINVAL, "non-finite value at %lld", (long long)k);
+            x[k] = E{r, A->col[k], v};
+            y[k] = E{A->col[k], r, v};
+        }
+    auto lt = [](const E& p, const E& q) { return p.a != q.a ? p.a < q.a : p.b < q.b; };
+    std::sort(x.begin(), x.end(), lt);
+    std::sort(y.begin(), y.end(), lt);
+    // sum duplicates then compare
+    auto fold = [](std::vector<E>& v) {
+        size_t o = 0;
+        for (size_t i = 0; i < v.size(); ++i) {
+            if (o && v[o - 1].a == v[i].a && v[o - 1].b == v[i].b) v[o - 1].v += v[i].v;
+            else v[o++] = v[i];
+        }
+        v.resize(o);
+    };
+    fold(x);
+    fold(y);
+    if (x.size() != y.size()) return fail(ctx, EVC_EINVAL, "matrix is not structurally symmetric");
+    for (size_t i = 0; i < x.size(); ++i) {
+        if (x[i].a != y[i].a || x[i].b != y[i].b)
+            return fail(ctx, EVC_EINVAL, "matrix is not structurally symmetric");
+        const double tolv = 1e-12 * std::max(std::fabs(x[i].v), std::fabs(y[i].v));
+        if (std::fabs(x[i].v - y[i].v) > tolv) return fail(ctx, EVC_EINVAL, "matrix is not symmetric");
+    }
+    return EVC_OK;
+}
+
+evc_ctx* new_ctx(int precision, void* stream)
+{
+    evc_ctx* c = new (std::nothrow) evc_ctx();
+    if (!c) return nullptr;
+    c->precision = precision;
+    c->tsize = precision == EVC_MIXED ? 4 : 8;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (!c->stream) {
+        // The legacy default stream cannot be captured into a graph: run on a
+        // private blocking stream, which the legacy stream still orders with.
+        if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return nullptr;
+        }
+        c->own_stream = true;
+    }
+    return c;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+int evc_version(void) { return 10000; }
+
+int evc_create_csr(const evc_csr* A, int precision, void* stream, evc_ctx** out)
+{
+    if (!out) return EVC_EINVAL;
+    *out = nullptr;
+    if (!A || (precision != EVC_FP64 && precision != EVC_MIXED)) return EVC_EINVAL;
+    if (A->n < 1 || A->n >= ((int64_t)1 << 31) || A->nnz < 0 || !A->row_ptr ||
+        (A->nnz > 0 && (!A->col || !A->val)))
+        return EVC_EINVAL;
+    evc_ctx* ctx = new_ctx(precision, stream);
+    if (!ctx) return EVC_ENOMEM;
+    ctx->op = OP_CSR;
+    ctx->n = A->n;
+    ctx->nnz = A->nnz;
+    int rc = EVC_OK;
+    if (!A->on_device && A->check) rc = validate_csr_host(ctx, A);
+    auto cleanup = [&](int code) {
+        evc_destroy(ctx);
+        return code;
+    };
+    if (rc) return cleanup(rc);
+    const int64_t n = A->n, nnz = A->nnz;
+    auto dmalloc = [&](void** p, size_t b) -> int {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(b, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return EVC_ENOMEM;
+        }
+        return EVC_OK;
+    };
+    if (A->on_device) {
+        ctx->csr.row_ptr = A->row_ptr;
+        ctx->csr.col = A->col;
+    } else {
+        if (dmalloc(&ctx->own_rowptr, (n + 1) * 8) || dmalloc(&ctx->own_col, nnz * 4))
+            return cleanup(EVC_ENOMEM);
+        if (cudaMemcpyAsync(ctx->own_rowptr, A->row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, ctx->stream) ||
+            cudaMemcpyAsync(ctx->own_col, A->col, nnz * 4, cudaMemcpyHostToDevice, ctx->stream))
+            return cleanup(EVC_ECUDA);
+        ctx->csr.row_ptr = static_cast<const int64_t*>(ctx->own_rowptr);
+        ctx->csr.col = static_cast<const int32_t*>(ctx->own_col);
+    }
+    const bool same = (A->val_is_fp32 ? 4u : 8u) == ctx->tsize;
+    if (A->on_device && same) {
+        ctx->csr.val = A->val;
+    } else {
+        if (dmalloc(&ctx->own_val, nnz * ctx->tsize)) return cleanup(EVC_ENOMEM);
+        rc = upload_values(ctx, ctx->own_val, A->val, nnz, A->val_is_fp32, A->on_device);
+        if (rc) return cleanup(rc);
+        ctx->csr.val = ctx->own_val;
+    }
+    ctx->csr.n = n;
+    ctx->csr.nnz = nnz;
+    if (dmalloc(reinterpret_cast<void**>(&ctx->own_diag), n * 8)) return cleanup(EVC_ENOMEM);
+    csr_diag_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, ctx->stream>>>(
+        ctx->csr.row_ptr, ctx->csr.col, A->on_device ? A->val : ctx->csr.val,
+        A->on_device ? A->val_is_fp32 : (ctx->tsize == 4), ctx->own_diag, n);
+    if (cudaGetLastError() != cudaSuccess) return cleanup(EVC_ECUDA);
+    ctx->csr.diag = ctx->own_diag;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(EVC_ECUDA);
+    *out = ctx;
+    return EVC_OK;
+}
+
+int evc_create_stencil(int N, double h, int order, const void* V, int V_is_fp32, int on_device,
+                       int precision, void* stream, evc_ctx** out)
+{
+    if (!out) return EVC_EINVAL;
+    *out = nullptr;
+    if ((precision != EVC_FP64 && precision != EVC_MIXED) || !V || !(h > 0.0) ||
+        !std::isfinite(h) || (order != 2 && order != 4))
+        return EVC_EINVAL;
+    if (N < (order == 2 ? 2 : 5) || (int64_t)N * N * N >= ((int64_t)1 << 31)) return EVC_EINVAL;
+    evc_ctx* ctx = new_ctx(precision, stream);
+    if (!ctx) return EVC_ENOMEM;
+    ctx->op = OP_STENCIL;
+    ctx->n = (int64_t)N * N * N;
+    StencilOp& s = ctx->sten;
+    s.N = N;
+    s.order = order;
+    s.h = h;
+    const double ih2 = 1.0 / (h * h);
+    if (order == 2) {
+        s.c1 = -0.5 * ih2;
+        s.c2 = 0.0;
+        s.cd = 3.0 * ih2;
+    } else {
+        s.c1 = -16.0 / 24.0 * ih2;
+        s.c2 = 1.0 / 24.0 * ih2;
+        s.cd = 90.0 / 24.0 * ih2;
+    }
+    const bool same = (V_is_fp32 ? 4u : 8u) == ctx->tsize;
+    if (on_device && same) {
+        s.V = V;
+    } else {
+        if (cudaMalloc(&ctx->own_V, ctx->n * ctx->tsize) != cudaSuccess) {
+            cudaGetLastError();
+            evc_destroy(ctx);
+            return EVC_ENOMEM;
+        }
+        int rc = upload_values(ctx, ctx->own_V, V, ctx->n, V_is_fp32, on_device);
+        if (rc == EVC_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = EVC_ECUDA;
+        if (rc) {
+            evc_destroy(ctx);
+            return rc;
+        }
+        s.V = ctx->own_V;
+    }
+    *out = ctx;
+    return EVC_OK;
+}
+
+int evc_set_values(evc_ctx* ctx, const void* values, int on_device)
+{
+    if (!ctx || !values) return EVC_EINVAL;
+    void* dst = ctx->op == OP_STENCIL ? ctx->own_V : ctx->own_val;
+    if (!dst) return fail(ctx, EVC_EINVAL, "values were borrowed at creation; update them in place");
+    const int64_t cnt = ctx->op == OP_STENCIL ? ctx->n : ctx->nnz;
+    const int fp32 = ctx->tsize == 4;
+    int rc = upload_values(ctx, dst, values, cnt, fp32, on_device);
+    if (rc) return rc;
+    if (ctx->op == OP_CSR) {
+        csr_diag_kernel<<<(int)std::min<int64_t>((ctx->n + 255) / 256, 152 * 16), 256, 0,
+                          ctx->stream>>>(ctx->csr.row_ptr, ctx->csr.col, ctx->csr.val, fp32,
+                                         ctx->own_diag, ctx->n);
+        CU(cudaGetLastError());
+    }
+    return EVC_OK;
+}
+
+int evc_set_precond(evc_ctx* ctx, int kind, double param0, double param1)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (kind == EVC_PREC_IDENTITY) {
+        ctx->prec = kind;
+    } else if (kind == EVC_PREC_JACOBI) {
+        if (!(param0 > 0.0) || !std::isfinite(param0))
+            return fail(ctx, EVC_EINVAL, "Jacobi eps must be > 0");
+        ctx->prec = kind;
+        ctx->jac_eps = param0;
+    } else if (kind == EVC_PREC_CHEB_KINETIC) {
+        if (ctx->op != OP_STENCIL)
+            return fail(ctx, EVC_EUNSUPPORTED, "the kinetic Chebyshev preconditioner needs a stencil context");
+        const int d = (int)param0;
+        if ((double)d != param0 || d < 1 || d > 32)
+            return fail(ctx, EVC_EINVAL, "Chebyshev degree must be an integer in [1, 32]");
+        if (!(param1 > 0.0) || !std::isfinite(param1))
+            return fail(ctx, EVC_EINVAL, "kinetic shift c must be > 0");
+        const StencilOp& s = ctx->sten;
+        const double a = param1;
+        const double b = param1 + (s.order == 2 ? 6.0 : 8.0) / (s.h * s.h);
+        std::vector<double> coef(d + 1);
+        evc::cheb_coefficients(d, a, b, coef.data());
+        // T = M^2 is SPD iff p_d > 0 on the spectrum of K: the periodic
+        // stencil's eigenvalues are c + sum over axes of the axis symbol at
+        // theta = 2 pi k / N.
+        const int N = s.N;
+        std::vector<double> sym(N);
+        for (int k = 0; k < N; ++k) sym[k] = axis_symbol(s.order, s.h, 2.0 * M_PI * k / N);
+        std::sort(sym.begin(), sym.end());
+        sym.erase(std::unique(sym.begin(), sym.end()), sym.end());
+        double pmin = 1e300;
+        for (size_t i1 = 0; i1 < sym.size(); ++i1)
+            for (size_t i2 = i1; i2 < sym.size(); ++i2)
+                for (size_t i3 = i2; i3 < sym.size(); ++i3)
+                    pmin = std::min(pmin, cheb_eval(coef, a, b, a + sym[i1] + sym[i2] + sym[i3]));
+        if (!(pmin > 0.0))
+            return fail(ctx, EVC_EINVAL, "Chebyshev preconditioner not positive on spec(K) (min %g)", pmin);
+        ctx->prec = kind;
+        ctx->cheb_degree = d;
+        ctx->cheb_c = param1;
+        ctx->cheb_a = a;
+        ctx->cheb_b = b;
+        ctx->cheb_coef = coef;
+    } else {
+        return fail(ctx, EVC_EINVAL, "unknown preconditioner kind %d", kind);
+    }
+    ++ctx->prec_version;
+    return EVC_OK;
+}
+
+size_t evc_workspace_bytes(const evc_ctx* ctx, int nshift, int nprobe, int maxsteps)
+{
+    if (!ctx || nshift < 1 || nprobe < 1 || maxsteps < 1 || maxsteps > EVC_MAX_STEPS) return 0;
+    const int kmax = (int)std::min<int64_t>(maxsteps, ctx->n);
+    return layout(ctx, nshift, nprobe, kmax).total;
+}
+
+int evc_set_workspace(evc_ctx* ctx, void* dptr, size_t bytes)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (dptr && ((uintptr_t)dptr & 255)) return fail(ctx, EVC_EINVAL, "workspace must be 256-byte aligned");
+    drop_graph(ctx);
+    if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = dptr;
+    ctx->ws_bytes = dptr ? bytes : 0;
+    ctx->ws_owned = false;
+    ctx->have_run = false;
+    return EVC_OK;
+}
+
+int evc_count_slices_async(evc_ctx* ctx, const double* shifts, int nshift, int nprobe,
+                           int maxsteps, double tol, uint64_t seed, double* d_n_below,
+                           double* d_quad, int* d_steps)
+{
+    int rc = run_async(ctx, shifts, nshift, nprobe, maxsteps, tol, seed);
+    if (rc) return rc;
+    const Run& r = ctx->run;
+    if (d_quad)
+        CU(cudaMemcpyAsync(d_quad, r.quad_final, (size_t)r.ncol_real * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_n_below)
+        CU(cudaMemcpyAsync(d_n_below, r.Lfinal, (size_t)r.S * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_steps)
+        CU(cudaMemcpyAsync(d_steps, r.steps, (size_t)r.S * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    return EVC_OK;
+}
+
+int evc_sync(evc_ctx* ctx)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (!ctx->have_run) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        return EVC_OK;
+    }
+    return check_device_error(ctx);
+}
+
+int evc_count_slices(evc_ctx* ctx, const double* shifts, int nshift, int nprobe, int maxsteps,
+                     double tol, uint64_t seed, double* n_below, double* per_probe_quad,
+                     int* steps_used)
+{
+    int rc = run_async(ctx, shifts, nshift, nprobe, maxsteps, tol, seed);
+    if (rc) return rc;
+    const Run& r = ctx->run;
+    const size_t need = (size_t)r.ncol_real * 8 + (size_t)r.S * 12 + 64;
+    rc = ensure_pinned(ctx, &ctx->pinres, &ctx->pinres_bytes, need);
+    if (rc) return rc;
+    char* h = static_cast<char*>(ctx->pinres);
+    double* hq = reinterpret_cast<double*>(h);
+    double* hL = hq + r.ncol_real;
+    int* hs = reinterpret_cast<int*>(hL + r.S);
+    CU(cudaMemcpyAsync(hq, r.quad_final, (size_t)r.ncol_real * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hL, r.Lfinal, (size_t)r.S * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hs, r.steps, (size_t)r.S * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    rc = check_device_error(ctx);
+    if (rc) return rc;
+    if (per_probe_quad) memcpy(per_probe_quad, hq, (size_t)r.ncol_real * 8);
+    if (n_below) memcpy(n_below, hL, (size_t)r.S * 8);
+    if (steps_used) memcpy(steps_used, hs, (size_t)r.S * 4);
+    return EVC_OK;
+}
+
+int evc_count(evc_ctx* ctx, double xi, double eta, int nprobe, int maxsteps, double tol,
+              uint64_t seed, double* estimate, double* per_probe_quad, int* steps_used)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (!(xi < eta)) return fail(ctx, EVC_EINVAL, "need xi < eta");
+    const double sh[2] = {xi, eta};
+    double L[2];
+    int rc = evc_count_slices(ctx, sh, 2, nprobe, maxsteps, tol, seed, L, per_probe_quad, steps_used);
+    if (rc) return rc;
+    if (estimate) *estimate = L[1] - L[0];
+    return EVC_OK;
+}
+
+int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (!ctx->have_run) return fail(ctx, EVC_EINVAL, "no previous run");
+    const Run& r = ctx->run;
+    const int K = r.kmax, nc = r.ncol, ncr = r.ncol_real;
+    std::vector<double> a((size_t)K * nc), b((size_t)(K + 1) * nc);
+    std::vector<int> kd(nc);
+    CU(cudaMemcpyAsync(a.data(), r.alpha, a.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(b.data(), r.beta, b.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(kd.data(), r.kdone, kd.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < ncr; ++c) {
+        const int done = kd[c];
+        if (kdone) kdone[c] = done;
+        for (int i = 0; i < K; ++i) {
+            if (alpha) alpha[(size_t)c * K + i] = i < done ? a[(size_t)i * nc + c] : 0.0;
+            if (beta) beta[(size_t)c * (K + 1) + i] = i <= done ? b[(size_t)i * nc + c] : 0.0;
+        }
+        if (beta) beta[(size_t)c * (K + 1) + K] = K <= done ? b[(size_t)K * nc + c] : 0.0;
+    }
+    return EVC_OK;
+}
+
+int evc_set_option(evc_ctx* ctx, int option, int64_t value)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (option == EVC_OPT_GRAPH) {
+        ctx->use_graph = value != 0;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_PROFILE) {
+        ctx->profile = value != 0;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    return fail(ctx, EVC_EINVAL, "unknown option %d", option);
+}
+
+int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (nrec) *nrec = (int)ctx->recs.size();
+    if (!recs || cap <= 0) return EVC_OK;
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int cnt = std::min<int>(cap, (int)ctx->recs.size());
+    for (int i = 0; i < cnt; ++i) {
+        const evc_ctx::Rec& r = ctx->recs[i];
+        recs[i].kind = r.kind;
+        recs[i].step = r.step;
+        recs[i].bytes = r.bytes;
+        float ms = -1.0f;
+        if (r.e0 && r.e1) CU(cudaEventElapsedTime(&ms, r.e0, r.e1));
+        recs[i].ms = ms;
+    }
+    return EVC_OK;
+}
+
+const char* evc_last_error(const evc_ctx* ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+void evc_destroy(evc_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
+    if (ctx->own_rowptr) cudaFree(ctx->own_rowptr);
+    if (ctx->own_col) cudaFree(ctx->own_col);
+    if (ctx->own_val) cudaFree(ctx->own_val);
+    if (ctx->own_diag) cudaFree(ctx->own_diag);
+    if (ctx->own_V) cudaFree(ctx->own_V);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->pinres) cudaFreeHost(ctx->pinres);
+    if (ctx->param_ev) cudaEventDestroy(ctx->param_ev);
+    for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// evc_internal.cuh -- internal declarations shared by the libevc translation
+// units (kernels + host orchestration). Not part of the C ABI.
+//
+// Data layout in HBM.  The (shift x probe) columns of one call are packed as
+// c = s*m + j and padded to a multiple of CW = 32.  A "chunk" is CW columns;
+// every block vector is stored chunk-major, row-major inside a chunk:
+//     X[chunk][row][CW]      (the CW probes of a row are contiguous)
+// so one grid point / CSR row of one chunk is one 128-byte (FP32) or
+// 256-byte (FP64) segment, and chunks whose shift has stopped early are
+// skipped as whole contiguous blocks.  The Lanczos basis of chunk ch is
+//     P[ch][slot][row][CW],  slot j holding the unnormalised q_{j+1},
+// with per-column scales s_j (q_{j+1} = s_j P_j), so normalisation costs no
+// extra pass over the vectors.  Per-column scalars are stored [step][column].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace evc {
+
+constexpr int CW = 32;                 // columns per chunk
+constexpr int kMaxSteps = 256;         // == EVC_MAX_STEPS
+constexpr int kThreads = 256;          // threads per block of the streaming kernels
+
+// Device-side error codes (mirror evc_status).
+enum { DERR_NONE = 0, DERR_NUMERIC = 4 };
+
+// One run (a call of evc_count_slices) -- device pointers and sizes.
+struct Run {
+    int64_t n;
+    int S, m, kmax;          // shifts, probes, steps (kmax already clamped)
+    int ncol, ncol_real;     // padded / real columns
+    int nchunk;
+    int nblk;                // row blocks per chunk in the reorth kernels
+    int64_t slot_stride;     // n*CW elements
+    int64_t chunk_stride;    // (kmax+1)*n*CW elements
+    void* basis;             // T[nchunk][kmax+1][n][CW]
+    // per column
+    double* sigma;           // [ncol]
+    int* shift_of;           // [ncol]
+    int64_t* probe_id;       // [ncol]
+    double* alpha;           // [kmax][ncol]
+    double* beta;            // [kmax+1][ncol]
+    double* scl;             // [kmax+1][ncol]
+    double* g;               // [kmax][ncol]
+    double* ppc;             // [ncol]
+    double* colscale;        // [ncol]
+    int* kdone;              // [ncol]
+    double* quad;            // [ncol]  latest quadrature
+    double* quad_final;      // [ncol]  quadrature at the shift's stop step
+    // per shift
+    double* shifts;          // [S]
+    double* Lprev;           // [S]
+    double* Lfinal;          // [S]
+    int* steps;              // [S]
+    int* sdone;              // [S]
+    int* chunk_active;       // [nchunk]
+    int* err;                // [1]
+    double* part_dot;        // [nchunk][nblk][kmax][CW]
+    double* part_nrm;        // [nchunk][nblk][CW]
+    double* eigw;            // [3][kmax][ncol]  eigensolver scratch
+    void* jac;               // T[S][n]  (Jacobi scales, when used)
+    // device scalars, rewritten before each replay
+    uint64_t* seed;          // [1]
+    double* tol;             // [1]
+    double breakdown_rel;
+};
+
+// Coefficients of one stencil pass (see evc_stencil.cu):
+//   st  = k1 * (L in)_offdiag + (k1*cd + k0 + [V_p] - [sigma_c]) * in_p
+//   (Jacobi variant: in is scaled by M on load and st by M_p)
+//   out = insc_c * st + a0 * xs_c * x_p - a2 * prev_p - ppc_c * pp_p
+struct StencilPass {
+    const void* in;   int64_t in_cs;
+    const void* x;    int64_t x_cs;
+    const void* prev; int64_t prev_cs;
+    const void* pp;   int64_t pp_cs;
+    void* out;        int64_t out_cs;
+    const double* insc;     // per column or null
+    const double* xs;       // per column or null
+    const double* ppc;      // per column or null
+    double k1, k0, a0, a2;
+    int useV, useSigma;
+};
+
+struct StencilOp {
+    int N, order;
+    double h;
+    double c1, c2, cd;      // L = -1/2 Lap_h: +-1 neighbours, +-2 neighbours, diagonal
+    const void* V;          // T[n]
+};
+
+struct CsrOp {
+    int64_t n, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;        // T[nnz]
+    const double* diag;     // double[n]
+};
+
+// Kernel launchers (T = float for EVC_MIXED, double for EVC_FP64).
+template <typename T>
+cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const StencilPass& p,
+                                bool jacobi, cudaStream_t st);
+template <typename T>
+cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, cudaStream_t st);
+cudaError_t launch_init_state(const Run& r, cudaStream_t st);
+template <typename T>
+cudaError_t launch_init_probe(const Run& r, cudaStream_t st);
+template <typename T>
+cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V, double vdiag,
+                                 double eps, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dots(const Run& r, int i, cudaStream_t st);
+cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update(const Run& r, int i, cudaStream_t st);
+cudaError_t launch_finish(const Run& r, int i, bool do_quad, bool last, cudaStream_t st);
+cudaError_t launch_active(const Run& r, cudaStream_t st);
+
+// Host-side helpers.
+int cheb_coefficients(int degree, double a, double b, double* coef);
+
+}  // namespace evc

@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libevc (include/evc.h).
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+library.  Functions keep the C names; ``Context`` is a small convenience
+wrapper that owns an ``evc_ctx*`` and hands torch-allocated device scratch to
+the library (PyTorch is used for device memory and streams only).
+
+Importing this module does not load the library; the first call does, and it
+raises ``RuntimeError`` if ``libevc.so`` is missing or cannot be loaded --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libevc.so")
+_lock = threading.Lock()
+_lib = None
+
+EVC_OK, EVC_EINVAL, EVC_ENOMEM, EVC_ECUDA, EVC_ENUMERIC, EVC_ETIMEOUT, EVC_EUNSUPPORTED = range(7)
+EVC_FP64, EVC_MIXED = 0, 1
+EVC_PREC_IDENTITY, EVC_PREC_JACOBI, EVC_PREC_CHEB_KINETIC = 0, 1, 2
+EVC_OPT_GRAPH, EVC_OPT_PROFILE = 1, 2
+(EVC_K_INIT, EVC_K_JACOBI, EVC_K_STENCIL, EVC_K_CSR, EVC_K_DOTS, EVC_K_REDUCE, EVC_K_UPDATE,
+ EVC_K_FINISH) = range(8)
+KERNEL_NAMES = ["init", "jacobi", "stencil", "csr", "dots", "reduce", "update", "finish"]
+EVC_MAX_STEPS = 256
+
+# Symbols declared in include/evc.h, in declaration order.
+EXPORTED = [
+    "evc_create_csr", "evc_create_stencil", "evc_set_values", "evc_set_precond",
+    "evc_workspace_bytes", "evc_set_workspace", "evc_count", "evc_count_slices",
+    "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_set_option",
+    "evc_get_profile", "evc_last_error", "evc_destroy", "evc_version",
+]
+
+
+class EvcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"evc error {code}: {msg}")
+        self.code = code
+
+
+class evc_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("val_is_fp32", C.c_int32),
+                ("on_device", C.c_int32), ("check", C.c_int32), ("reserved", C.c_int32)]
+
+
+class evc_prof_rec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("step", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libevc.so (once) and declare the C signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libevc.so not built ({p}); run __graft_entry__.build()")
+        lib = C.CDLL(p)
+        vp, d, i32, i64, u64 = C.c_void_p, C.c_double, C.c_int, C.c_int64, C.c_uint64
+        pp = C.POINTER(C.c_void_p)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int)
+        sig = {
+            "evc_create_csr": (i32, [C.POINTER(evc_csr), i32, vp, pp]),
+            "evc_create_stencil": (i32, [i32, d, i32, vp, i32, i32, i32, vp, pp]),
+            "evc_set_values": (i32, [vp, vp, i32]),
+            "evc_set_precond": (i32, [vp, i32, d, d]),
+            "evc_workspace_bytes": (C.c_size_t, [vp, i32, i32, i32]),
+            "evc_set_workspace": (i32, [vp, vp, C.c_size_t]),
+            "evc_count": (i32, [vp, d, d, i32, i32, d, u64, dp, dp, ip]),
+            "evc_count_slices": (i32, [vp, dp, i32, i32, i32, d, u64, dp, dp, ip]),
+            "evc_count_slices_async": (i32, [vp, dp, i32, i32, i32, d, u64, vp, vp, vp]),
+            "evc_sync": (i32, [vp]),
+            "evc_get_tridiag": (i32, [vp, dp, dp, ip]),
+            "evc_set_option": (i32, [vp, i32, i64]),
+            "evc_get_profile": (i32, [vp, C.POINTER(evc_prof_rec), i32, ip]),
+            "evc_last_error": (C.c_char_p, [vp]),
+            "evc_destroy": (None, [vp]),
+            "evc_version": (i32, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _check(ctx, rc):
+    if rc != EVC_OK:
+        msg = load().evc_last_error(ctx).decode() if ctx else ""
+        raise EvcError(rc, msg)
+
+
+# ----------------------------------------------------------- C-named calls
+
+def evc_create_csr(row_ptr, col, val, precision=EVC_FP64, stream=None, check=True, on_device=False):
+    """row_ptr/col/val: numpy arrays (host) or torch CUDA tensors (on_device=True)."""
+    lib = load()
+    keep = []
+    if on_device:
+        n = int(row_ptr.numel()) - 1
+        nnz = int(col.numel())
+        a = evc_csr(n, nnz, row_ptr.data_ptr(), col.data_ptr(), val.data_ptr(),
+                    1 if str(val.dtype) == "torch.float32" else 0, 1, 0, 0)
+    else:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col, dtype=np.int32)
+        fp32 = np.asarray(val).dtype == np.float32
+        va = np.ascontiguousarray(val, dtype=np.float32 if fp32 else np.float64)
+        keep += [rp, ci, va]
+        a = evc_csr(len(rp) - 1, len(ci), rp.ctypes.data, ci.ctypes.data, va.ctypes.data,
+                    1 if fp32 else 0, 0, 1 if check else 0, 0)
+    out = C.c_void_p()
+    rc = lib.evc_create_csr(C.byref(a), precision, stream, C.byref(out))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_create_csr failed")
+    return out.value
+
+
+def evc_create_stencil(N, h, order, V, precision=EVC_FP64, stream=None, on_device=False):
+    lib = load()
+    if on_device:
+        ptr, fp32 = V.data_ptr(), 1 if str(V.dtype) == "torch.float32" else 0
+    else:
+        fp32 = 1 if np.asarray(V).dtype == np.float32 else 0
+        Va = np.ascontiguousarray(V, dtype=np.float32 if fp32 else np.float64)
+        ptr = Va.ctypes.data
+    out = C.c_void_p()
+    rc = lib.evc_create_stencil(int(N), float(h), int(order), ptr, fp32, 1 if on_device else 0,
+                                precision, stream, C.byref(out))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_create_stencil failed")
+    return out.value
+
+
+def evc_set_values(ctx, values_ptr, on_device):
+    _check(ctx, load().evc_set_values(ctx, values_ptr, 1 if on_device else 0))
+
+
+def evc_set_precond(ctx, kind, p0=0.0, p1=0.0):
+    _check(ctx, load().evc_set_precond(ctx, kind, float(p0), float(p1)))
+
+
+def evc_workspace_bytes(ctx, nshift, nprobe, maxsteps):
+    return int(load().evc_workspace_bytes(ctx, nshift, nprobe, maxsteps))
+
+
+def evc_set_workspace(ctx, dptr, nbytes):
+    _check(ctx, load().evc_set_workspace(ctx, dptr, nbytes))
+
+
+def evc_count(ctx, xi, eta, nprobe, maxsteps, tol=0.0, seed=0):
+    est = np.zeros(1)
+    quad = np.zeros(2 * nprobe)
+    steps = np.zeros(2, dtype=np.int32)
+    _check(ctx, load().evc_count(ctx, xi, eta, nprobe, maxsteps, tol, C.c_uint64(seed),
+                                 _dp(est), _dp(quad), _ip(steps)))
+    return float(est[0]), quad.reshape(2, nprobe), steps
+
+
+def evc_count_slices(ctx, shifts, nprobe, maxsteps, tol=0.0, seed=0):
+    sh = np.ascontiguousarray(shifts, dtype=np.float64)
+    S = sh.size
+    L = np.zeros(S)
+    quad = np.zeros(S * nprobe)
+    steps = np.zeros(S, dtype=np.int32)
+    _check(ctx, load().evc_count_slices(ctx, _dp(sh), S, nprobe, maxsteps, tol, C.c_uint64(seed),
+                                        _dp(L), _dp(quad), _ip(steps)))
+    return L, quad.reshape(S, nprobe), steps
+
+
+def evc_count_slices_async(ctx, shifts, nprobe, maxsteps, tol, seed, d_n_below, d_quad, d_steps):
+    sh = np.ascontiguousarray(shifts, dtype=np.float64)
+    _check(ctx, load().evc_count_slices_async(ctx, _dp(sh), sh.size, nprobe, maxsteps, tol,
+                                              C.c_uint64(seed), d_n_below, d_quad, d_steps))
+
+
+def evc_sync(ctx):
+    _check(ctx, load().evc_sync(ctx))
+
+
+def evc_get_tridiag(ctx, ncol, maxsteps):
+    a = np.zeros(ncol * maxsteps)
+    b = np.zeros(ncol * (maxsteps + 1))
+    kd = np.zeros(ncol, dtype=np.int32)
+    _check(ctx, load().evc_get_tridiag(ctx, _dp(a), _dp(b), _ip(kd)))
+    return a.reshape(ncol, maxsteps), b.reshape(ncol, maxsteps + 1), kd
+
+
+def evc_set_option(ctx, option, value):
+    _check(ctx, load().evc_set_option(ctx, option, int(value)))
+
+
+def evc_get_profile(ctx):
+    """Launch list of the last call: list of (kind, step, ms, bytes)."""
+    lib = load()
+    n = C.c_int(0)
+    _check(ctx, lib.evc_get_profile(ctx, None, 0, C.byref(n)))
+    recs = (evc_prof_rec * max(1, n.value))()
+    _check(ctx, lib.evc_get_profile(ctx, recs, n.value, C.byref(n)))
+    return [(r.kind, r.step, r.ms, r.bytes) for r in recs[:n.value]]
+
+
+def evc_last_error(ctx):
+    return load().evc_last_error(ctx).decode()
+
+
+def evc_destroy(ctx):
+    if ctx:
+        load().evc_destroy(ctx)
+
+
+def evc_version():
+    return int(load().evc_version())
+
+
+# ------------------------------------------------------------- convenience
+
+class Context:
+    """Owns an evc_ctx*; optionally backs its scratch with a torch CUDA buffer."""
+
+    def __init__(self, handle, torch_workspace=True):
+        self.h = handle
+        self._ws = None
+        self._torch_ws = torch_workspace
+
+    @classmethod
+    def csr(cls, csr, precision=EVC_FP64, stream=None, **kw):
+        return cls(evc_create_csr(*csr, precision=precision, stream=stream), **kw)
+
+    @classmethod
+    def stencil(cls, N, h, order, V, precision=EVC_FP64, stream=None, **kw):
+        return cls(evc_create_stencil(N, h, order, V, precision=precision, stream=stream), **kw)
+
+    def set_precond(self, kind, p0=0.0, p1=0.0):
+        evc_set_precond(self.h, kind, p0, p1)
+        return self
+
+    def reserve(self, nshift, nprobe, maxsteps):
+        """Allocate the library's scratch from the torch caching allocator."""
+        need = evc_workspace_bytes(self.h, nshift, nprobe, maxsteps)
+        if self._torch_ws and (self._ws is None or self._ws.numel() < need):
+            import torch
+            self._ws = None
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+            ptr = self._ws.data_ptr()
+            aligned = (ptr + 255) & ~255
+            evc_set_workspace(self.h, aligned, need + 256 - (aligned - ptr))
+
+    def count(self, xi, eta, nprobe, maxsteps, tol=0.0, seed=0):
+        self.reserve(2, nprobe, maxsteps)
+        return evc_count(self.h, xi, eta, nprobe, maxsteps, tol, seed)
+
+    def count_slices(self, shifts, nprobe, maxsteps, tol=0.0, seed=0):
+        self.reserve(len(shifts), nprobe, maxsteps)
+        return evc_count_slices(self.h, shifts, nprobe, maxsteps, tol, seed)
+
+    def tridiag(self, ncol, maxsteps):
+        return evc_get_tridiag(self.h, ncol, maxsteps)
+
+    def close(self):
+        if self.h:
+            evc_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,102 @@
+"""Named synthetic workloads (shapes, sizes, seeds, shifts) used by the
+benchmark and the full-size parity tests.
+
+Each workload is the input recipe only: the matrix comes from ``inputs``, the
+shifts are fixed numbers recorded here with how they were obtained.  Nothing
+here computes any part of the estimator.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs as I
+
+
+@dataclass
+class Workload:
+    name: str
+    kind: str                     # "stencil" or "csr"
+    shifts: list
+    nprobe: int
+    maxsteps: int
+    tol: float = 0.0
+    precond: str = "identity"     # identity | jacobi | cheb
+    prec_params: tuple = (0.0, 0.0)
+    N: int = 0
+    h: float = 0.0
+    order: int = 2
+    csr_builder: object = None
+    nwells: int = 32
+    seed: int = 0
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        if self.kind == "stencil":
+            return self.N ** 3
+        return self.notes["n"]
+
+    def potential(self) -> np.ndarray:
+        return I.gaussian_wells(self.N, self.h, nwells=self.nwells, seed=1)
+
+    def csr(self):
+        return self.csr_builder()
+
+
+# Lowest eigenvalue of H = -1/2 Lap_h + V on the periodic 64^3 grid (7-point,
+# h = 0.3, 32 wells, well seed 1) by scipy.sparse.linalg.eigsh (ARPACK,
+# which='SA', tol 1e-10), and the 300th/301st eigenvalues by shift-invert
+# eigsh around lambda_min - 0.5 (320 eigenvalues, tol 1e-10).
+FD64_LAMBDA_MIN = -3.2826731738772574
+FD64_LAMBDA_300 = None
+FD64_LAMBDA_301 = None
+
+
+def fd64_eta() -> float:
+    if FD64_LAMBDA_300 is None:
+        return FD64_LAMBDA_MIN + 2.0
+    return 0.5 * (FD64_LAMBDA_300 + FD64_LAMBDA_301)
+
+
+def fd_hamiltonian_64() -> Workload:
+    """3D FD Hamiltonian, 7-point periodic 64^3 (n = 262,144), h = 0.3, 32
+    Gaussian wells; [lambda_min - 1, eta], eta between the 300th and 301st
+    eigenvalues; Chebyshev degree-8 kinetic preconditioner (c = 1); 64
+    probes (seed 0); 30 Lanczos steps."""
+    return Workload(name="fd_hamiltonian_64^3_7pt_cheb8_m64_k30", kind="stencil",
+                    shifts=[FD64_LAMBDA_MIN - 1.0, fd64_eta()], nprobe=64, maxsteps=30,
+                    precond="cheb", prec_params=(8, 1.0), N=64, h=0.3, order=2)
+
+
+def laplace32() -> Workload:
+    """2D Dirichlet 5-point Laplacian 32x32 (n = 1024), [1, 2], Jacobi, 16
+    probes, 40 steps, FP64."""
+    return Workload(name="laplace2d_32x32_jacobi_m16_k40", kind="csr", shifts=[1.0, 2.0],
+                    nprobe=16, maxsteps=40, precond="jacobi", prec_params=(1e-3, 0.0),
+                    csr_builder=lambda: I.laplace2d_dirichlet(32), notes={"n": 1024})
+
+
+def batched_slicing_96(lmin: float) -> Workload:
+    """4th-order 13-point periodic 96^3 (n = 884,736), 32 shifts
+    lambda_min + 8 s/32, 64 probes, tol 0.25, at most 30 steps, Chebyshev-8."""
+    return Workload(name="slicing_96^3_13pt_cheb8_S32_m64", kind="stencil",
+                    shifts=[lmin + 8.0 * s / 32 for s in range(1, 33)], nprobe=64, maxsteps=30,
+                    tol=0.25, precond="cheb", prec_params=(8, 1.0), N=96, h=0.3, order=4)
+
+
+def powerlaw_2m() -> Workload:
+    """Generic sparse symmetric n = 2,000,000, power-law rows (mean ~30),
+    [-0.5, 0.5], Jacobi, 128 probes, 50 steps."""
+    return Workload(name="powerlaw_2M_jacobi_m128_k50", kind="csr", shifts=[-0.5, 0.5],
+                    nprobe=128, maxsteps=50, precond="jacobi", prec_params=(1e-3, 0.0),
+                    csr_builder=lambda: I.powerlaw_symmetric(2_000_000, seed=2),
+                    notes={"n": 2_000_000})
+
+
+WORKLOADS = {
+    "fd64": fd_hamiltonian_64,
+    "laplace32": laplace32,
+    "powerlaw2m": powerlaw_2m,
+}
