@@ -183,6 +183,9 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.sdone = I(S);
     r.chunk_active = I(nchunk);
     r.part_dot = D((size_t)nchunk * nblk * kmax * CW);
+    r.part_gram = D((size_t)nchunk * nblk * kmax * CW);
+    r.hbuf = D((size_t)kmax * ncol);
+    r.gram = D((size_t)kmax * (kmax + 1) / 2 * ncol);
     r.part_nrm = D((size_t)nchunk * nblk * CW);
     r.eigw = D((size_t)3 * kmax * ncol);
     r.err = I(1);
@@ -506,8 +509,11 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         if (rc) return rc;
         rc = rec(ctx, EVC_K_DOTS, i, vec * (i + 1), [&] { return launch_dots<T>(r, i, st); });
         if (!rc)
-            rc = rec(ctx, EVC_K_REDUCE, i, (double)r.nchunk * r.nblk * i * CW * 8 + colb * 2 * i,
+            rc = rec(ctx, EVC_K_REDUCE, i, 2.0 * r.nchunk * r.nblk * i * CW * 8 + colb * 3 * i,
                      [&] { return launch_reduce(r, i, st); });
+        if (!rc)
+            rc = rec(ctx, EVC_K_REDUCE, i, colb * (2.0 * i + i * (i + 1) / 2),
+                     [&] { return launch_coef(r, i, st); });
         if (!rc)
             rc = rec(ctx, EVC_K_UPDATE, i, vec * (i + 2), [&] { return launch_update<T>(r, i, st); });
         const bool last = (i == r.kmax);

@@ -56,7 +56,10 @@ struct Run {
     int* sdone;              // [S]
     int* chunk_active;       // [nchunk]
     int* err;                // [1]
-    double* part_dot;        // [nchunk][nblk][kmax][CW]
+    double* part_dot;        // [nchunk][nblk][kmax][CW]  partial P_j . w
+    double* part_gram;       // [nchunk][nblk][kmax][CW]  partial P_j . P_{i-1}
+    double* hbuf;            // [kmax][ncol]  h_j = q_j . w of the current step
+    double* gram;            // [kmax(kmax+1)/2][ncol]  G_ab = q_a . q_b, a >= b
     double* part_nrm;        // [nchunk][nblk][CW]
     double* eigw;            // [3][kmax][ncol]  eigensolver scratch
     void* jac;               // T[S][n]  (Jacobi scales, when used)
@@ -113,6 +116,7 @@ cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
+cudaError_t launch_coef(const Run& r, int i, cudaStream_t st);
 template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_finish(const Run& r, int i, bool do_quad, bool last, cudaStream_t st);

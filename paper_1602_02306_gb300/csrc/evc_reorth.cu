@@ -3,14 +3,22 @@
 // quadrature (Eq. gauss_quad) and the per-shift estimator (Algorithm 2).
 //
 // Per step i, for every column c (w = C q_i - beta_i q_{i-1} is in slot i):
-//   dots    h_j = q_j^T w, j = 1..i           (partials per row block)
-//   reduce  alpha_i = h_i; g_j = h_j s_j       (FP64, fixed summation order)
-//   update  w <- w - sum_j g_j P_j = w - Q_i (Q_i^T w);  ||w||^2 partials
+//   dots    h_j = q_j^T w and G_ij = q_j^T q_i, j = 1..i, in one sweep over
+//           the basis (partials per row block)
+//   reduce  h, the new Gram row, alpha_i = h_i       (FP64, fixed order)
+//   coef    c = h + (I - G) h                        (FP64, per column)
+//   update  w <- w - Q_i c;  ||w||^2 partials
 //   finish  beta_{i+1} = ||w||, s_{i+1} = 1/beta_{i+1}, breakdown test,
 //           eig(J_i) -> quadrature, per-shift mean L(i) and stop rule.
-// In exact arithmetic the single fused classical Gram-Schmidt pass equals
-// Algorithm 1's "alpha_i = q_i^T w; w -= alpha_i q_i; w -= Q_i (Q_i^T w)",
-// since the second projection's i-th coefficient is then zero.
+// In exact arithmetic G = I, c = h, and the single fused classical
+// Gram-Schmidt sweep equals Algorithm 1's "alpha_i = q_i^T w;
+// w -= alpha_i q_i; w -= Q_i (Q_i^T w)" (the second projection's i-th
+// coefficient is then zero).  In floating point the stored basis is
+// orthonormal only to the working precision; the term (I - G) h is the
+// second Gram-Schmidt pass Q_i^T (w - Q_i h) = (I - G) h evaluated from the
+// Gram matrix instead of a second sweep over the vectors, which keeps the
+// FP32 basis as orthogonal as two full passes would (CGS2) at the cost of
+// one pass.  The Gram row of q_i is formed in the same sweep as Q_i^T w.
 //
 // Reductions are deterministic: per-thread partial sums over a fixed row
 // set (FP32 runs of 16 rows promoted to FP64 in mixed mode), a fixed
@@ -26,6 +34,7 @@ namespace {
 constexpr int JB = 8;          // basis vectors per pass of the dot kernel
 constexpr int RUN = 16;        // rows per FP32 partial-sum run
 constexpr int WARPS = kThreads / 32;
+static_assert(JB == WARPS, "the dot kernel's warp tree maps warp q to basis vector jg + q");
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z)
 {
@@ -101,52 +110,94 @@ __device__ __forceinline__ void row_range(int64_t n, int nblk, int blk, int64_t&
     r1 = min(n, r0 + per);
 }
 
-// part_dot[ch][blk][j][lane] = sum_{rows of blk} P_j[row][lane] * w[row][lane], j < i
+// part_dot[ch][blk][j][lane]  = sum_{rows of blk} P_j[row][lane] * w[row][lane]
+// part_gram[ch][blk][j][lane] = sum_{rows of blk} P_j[row][lane] * P_{i-1}[row][lane]
+// for j < i.  The block walks its rows in slabs of WARPS*RTD rows; each warp
+// holds RTD-row tiles of w and of P_{i-1} in registers and streams JB basis
+// tiles at a time against both (independent loads).  Tile sums (FP32 runs of
+// RTD rows in mixed mode) go through a fixed shared-memory tree into per-block
+// FP64 accumulators, so the summation order is fixed and w is read once.
+constexpr int RT = 16;          // rows per warp tile (update)
+constexpr int RTD = 8;          // rows per warp tile (dots)
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 reorth_dots_kernel(Run r, int i)
 {
     const int ch = blockIdx.y, blk = blockIdx.x;
     if (!r.chunk_active[ch]) return;
-    __shared__ double red[WARPS][JB][CW];
+    extern __shared__ double sm[];
+    double* bacc = sm;                              // [i][CW]
+    double* bgram = sm + (size_t)i * CW;            // [i][CW]
+    double* red = sm + (size_t)2 * i * CW;          // [WARPS][2*JB][CW]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < 2 * i * CW; e += blockDim.x) sm[e] = 0.0;
     int64_t r0, r1;
     row_range(r.n, r.nblk, blk, r0, r1);
-    const T* P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
-    const T* w = P + (int64_t)i * r.slot_stride;
-    typedef typename Acc<T>::run RT;
-    for (int jg = 0; jg < i; jg += JB) {
-        double acc[JB];
-        RT run[JB];
+    const T* __restrict__ P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
+    const T* __restrict__ w = P + (int64_t)i * r.slot_stride;
+    const T* __restrict__ q = P + (int64_t)(i - 1) * r.slot_stride;
+    typedef typename Acc<T>::run RTy;
+    for (int64_t base = r0; base < r1; base += (int64_t)WARPS * RTD) {
+        const int64_t t0 = base + (int64_t)warp * RTD;
+        T wv[RTD], qv[RTD];
 #pragma unroll
-        for (int jj = 0; jj < JB; ++jj) { acc[jj] = 0.0; run[jj] = 0; }
-        int cnt = 0;
-        for (int64_t row = r0 + warp; row < r1; row += WARPS) {
-            const T wv = __ldg(w + row * CW + lane);
+        for (int t = 0; t < RTD; ++t) {
+            const bool ok = t0 + t < r1;
+            wv[t] = ok ? __ldg(w + (t0 + t) * CW + lane) : (T)0;
+            qv[t] = ok ? __ldg(q + (t0 + t) * CW + lane) : (T)0;
+        }
+        for (int jg = 0; jg < i; jg += JB) {
+            RTy a[JB], b[JB];
 #pragma unroll
-            for (int jj = 0; jj < JB; ++jj)
-                if (jg + jj < i)
-                    run[jj] += __ldg(P + (int64_t)(jg + jj) * r.slot_stride + row * CW + lane) * wv;
-            if (++cnt == RUN) {
+            for (int jj = 0; jj < JB; ++jj) { a[jj] = 0; b[jj] = 0; }
 #pragma unroll
-                for (int jj = 0; jj < JB; ++jj) { acc[jj] += (double)run[jj]; run[jj] = 0; }
-                cnt = 0;
+            for (int jj = 0; jj < JB; ++jj) {
+                if (jg + jj < i) {
+                    const T* __restrict__ Pj = P + (int64_t)(jg + jj) * r.slot_stride + t0 * CW + lane;
+#pragma unroll
+                    for (int t = 0; t < RTD; ++t)
+                        if (t0 + t < r1) {
+                            const RTy pj = (RTy)__ldg(Pj + t * CW);
+                            a[jj] += pj * (RTy)wv[t];
+                            b[jj] += pj * (RTy)qv[t];
+                        }
+                }
             }
-        }
 #pragma unroll
-        for (int jj = 0; jj < JB; ++jj) red[warp][jj][lane] = acc[jj] + (double)run[jj];
-        __syncthreads();
-        if (warp < JB && jg + warp < i) {
-            double s = 0.0;
+            for (int jj = 0; jj < JB; ++jj) {
+                red[((size_t)warp * 2 * JB + jj) * CW + lane] = (double)a[jj];
+                red[((size_t)warp * 2 * JB + JB + jj) * CW + lane] = (double)b[jj];
+            }
+            __syncthreads();
+            if (jg + warp < i) {
+                double sa = 0.0, sb = 0.0;
 #pragma unroll
-            for (int q = 0; q < WARPS; ++q) s += red[q][warp][lane];
-            r.part_dot[(((int64_t)ch * r.nblk + blk) * r.kmax + jg + warp) * CW + lane] = s;
+                for (int qq = 0; qq < WARPS; ++qq) {
+                    sa += red[((size_t)qq * 2 * JB + warp) * CW + lane];
+                    sb += red[((size_t)qq * 2 * JB + JB + warp) * CW + lane];
+                }
+                bacc[(size_t)(jg + warp) * CW + lane] += sa;
+                bgram[(size_t)(jg + warp) * CW + lane] += sb;
+            }
+            __syncthreads();
         }
-        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < i * CW; e += blockDim.x) {
+        const int64_t o = (((int64_t)ch * r.nblk + blk) * r.kmax + e / CW) * CW + (e % CW);
+        r.part_dot[o] = bacc[e];
+        r.part_gram[o] = bgram[e];
     }
 }
 
-// h_j = s_j * sum_blk part_dot;  alpha_i = h_i;  g_j = h_j * s_j
+__device__ __forceinline__ int64_t tri(int a, int b)
+{
+    // packed lower triangle, a >= b
+    return (int64_t)a * (a + 1) / 2 + b;
+}
+
+// h_j = s_j * sum_blk part_dot;  G_{i-1,j} = s_{i-1} s_j * sum_blk part_gram;
+// alpha_i = h_{i-1}  (slot j holds q_{j+1})
 __global__ void reorth_reduce_kernel(Run r, int i)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,16 +205,40 @@ __global__ void reorth_reduce_kernel(Run r, int i)
     const int c = t % r.ncol, j = t / r.ncol;
     const int ch = c / CW, lane = c % CW;
     if (!r.chunk_active[ch]) return;
-    double s = 0.0;
-    for (int b = 0; b < r.nblk; ++b)
-        s += r.part_dot[(((int64_t)ch * r.nblk + b) * r.kmax + j) * CW + lane];
+    double sh = 0.0, sg = 0.0;
+    for (int b = 0; b < r.nblk; ++b) {
+        const int64_t o = (((int64_t)ch * r.nblk + b) * r.kmax + j) * CW + lane;
+        sh += r.part_dot[o];
+        sg += r.part_gram[o];
+    }
     const double sj = r.scl[(int64_t)j * r.ncol + c];
-    const double h = s * sj;
+    const double si = r.scl[(int64_t)(i - 1) * r.ncol + c];
+    const double h = sh * sj;
+    r.hbuf[(int64_t)j * r.ncol + c] = h;
+    r.gram[tri(i - 1, j) * r.ncol + c] = sg * sj * si;
     if (j == i - 1) r.alpha[(int64_t)(i - 1) * r.ncol + c] = h;
-    r.g[(int64_t)j * r.ncol + c] = h * sj;
 }
 
-// w <- w - sum_{j<i} g_j P_j (in place, slot i); part_nrm = partial ||w||^2
+// c = h + (I - G) h, g_j = c_j s_j (coefficients of the unnormalised P_j)
+__global__ void reorth_coef_kernel(Run r, int i)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= r.ncol) return;
+    if (!r.chunk_active[c / CW]) return;
+    for (int j = 0; j < i; ++j) {
+        double gh = 0.0;
+        for (int l = 0; l < i; ++l) {
+            const double G = r.gram[(j >= l ? tri(j, l) : tri(l, j)) * r.ncol + c];
+            gh += G * r.hbuf[(int64_t)l * r.ncol + c];
+        }
+        const double hj = r.hbuf[(int64_t)j * r.ncol + c];
+        r.g[(int64_t)j * r.ncol + c] = (2.0 * hj - gh) * r.scl[(int64_t)j * r.ncol + c];
+    }
+}
+
+// w <- w - sum_{j<i} g_j P_j (in place, slot i); part_nrm = partial ||w||^2.
+// Same warp tiling as the dot kernel: the w tile lives in registers while
+// every P_j tile streams past it.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 reorth_update_kernel(Run r, int i)
@@ -179,30 +254,32 @@ reorth_update_kernel(Run r, int i)
     __syncthreads();
     int64_t r0, r1;
     row_range(r.n, r.nblk, blk, r0, r1);
-    const T* P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
-    T* w = static_cast<T*>(r.basis) + ch * r.chunk_stride + (int64_t)i * r.slot_stride;
-    typedef typename Acc<T>::run RT;
+    const T* __restrict__ P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
+    T* __restrict__ w = static_cast<T*>(r.basis) + ch * r.chunk_stride + (int64_t)i * r.slot_stride;
+    typedef typename Acc<T>::run RTy;
     double acc = 0.0;
-    RT run = 0;
-    int cnt = 0;
-    for (int64_t row = r0 + warp; row < r1; row += WARPS) {
-        T wv = w[row * CW + lane];
-        int j = 0;
-        for (; j + JB <= i; j += JB) {
-            T pv[JB];
+    for (int64_t t0 = r0 + (int64_t)warp * RT; t0 < r1; t0 += (int64_t)WARPS * RT) {
+        T wv[RT];
 #pragma unroll
-            for (int jj = 0; jj < JB; ++jj)
-                pv[jj] = __ldg(P + (int64_t)(j + jj) * r.slot_stride + row * CW + lane);
+        for (int t = 0; t < RT; ++t) wv[t] = (t0 + t < r1) ? w[(t0 + t) * CW + lane] : (T)0;
+#pragma unroll 2
+        for (int j = 0; j < i; ++j) {
+            const T gj = gs[j * CW + lane];
+            const T* __restrict__ Pj = P + (int64_t)j * r.slot_stride + t0 * CW + lane;
 #pragma unroll
-            for (int jj = 0; jj < JB; ++jj) wv -= gs[(j + jj) * CW + lane] * pv[jj];
+            for (int t = 0; t < RT; ++t)
+                if (t0 + t < r1) wv[t] -= gj * __ldg(Pj + t * CW);
         }
-        for (; j < i; ++j)
-            wv -= gs[j * CW + lane] * __ldg(P + (int64_t)j * r.slot_stride + row * CW + lane);
-        w[row * CW + lane] = wv;
-        run += (RT)wv * (RT)wv;
-        if (++cnt == RUN) { acc += (double)run; run = 0; cnt = 0; }
+        RTy nr = 0;
+#pragma unroll
+        for (int t = 0; t < RT; ++t)
+            if (t0 + t < r1) {
+                w[(t0 + t) * CW + lane] = wv[t];
+                nr += (RTy)wv[t] * (RTy)wv[t];
+            }
+        acc += (double)nr;
     }
-    red[warp][lane] = acc + (double)run;
+    red[warp][lane] = acc;
     __syncthreads();
     if (warp == 0) {
         double s = 0.0;
@@ -409,7 +486,14 @@ cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st)
 {
-    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), kThreads, 0, st>>>(r, i);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(reorth_dots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((2 * kMaxSteps + 2 * WARPS * JB) * CW * sizeof(double)));
+        attr_set = true;
+    }
+    const size_t smem = ((size_t)2 * i + 2 * WARPS * JB) * CW * sizeof(double);
+    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), kThreads, smem, st>>>(r, i);
     return cudaGetLastError();
 }
 
@@ -417,6 +501,12 @@ cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st)
 {
     const int tot = r.ncol * i;
     reorth_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(r, i);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coef(const Run& r, int i, cudaStream_t st)
+{
+    reorth_coef_kernel<<<(r.ncol + 127) / 128, 128, 0, st>>>(r, i);
     return cudaGetLastError();
 }
 

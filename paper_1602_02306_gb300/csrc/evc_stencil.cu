@@ -65,7 +65,7 @@ struct KArgs {
 };
 
 template <typename T, int R, bool JAC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, R == 1 ? 4 : 3)
 stencil_pass_kernel(KArgs a)
 {
     constexpr int W = 16 / sizeof(T);        // columns per thread
@@ -73,6 +73,19 @@ stencil_pass_kernel(KArgs a)
     constexpr int TY = kThreads / LPP / TX;  // points per block along y
     const int ch = blockIdx.z;
     if (!a.chunk_active[ch]) return;
+    // per-column constants of this chunk, shared by the block
+    __shared__ Pack<T> s_sig[LPP], s_insc[LPP], s_a0s[LPP], s_ppc[LPP];
+    __shared__ int s_shift[CW];
+    if (threadIdx.x < CW) {
+        const int c = ch * CW + threadIdx.x;
+        const int l = threadIdx.x / W, w = threadIdx.x % W;
+        s_sig[l].v[w] = a.p.useSigma ? (T)a.sigma[c] : (T)0;
+        s_insc[l].v[w] = a.p.insc ? (T)a.p.insc[c] : (T)1;
+        s_a0s[l].v[w] = (T)(a.p.a0 * (a.p.xs ? a.p.xs[c] : 1.0));
+        s_ppc[l].v[w] = a.p.ppc ? (T)a.p.ppc[c] : (T)0;
+        s_shift[threadIdx.x] = JAC ? a.shift_of[c] : 0;
+    }
+    __syncthreads();
     const int N = a.op.N;
     const int lane = threadIdx.x % LPP;
     const int pt = threadIdx.x / LPP;
@@ -84,30 +97,18 @@ stencil_pass_kernel(KArgs a)
     const int z1 = min(z0 + ZB, N);
     const int64_t n = a.n;
 
-    const Pack<T>* in = reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* __restrict__ in = reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.in) + ch * a.p.in_cs) + lane;
-    const Pack<T>* xv = a.p.x ? reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* __restrict__ xv = a.p.x ? reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.x) + ch * a.p.x_cs) + lane : nullptr;
     const Pack<T>* pv = a.p.prev ? reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.prev) + ch * a.p.prev_cs) + lane : nullptr;
-    const Pack<T>* ppv = a.p.pp ? reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* __restrict__ ppv = a.p.pp ? reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.pp) + ch * a.p.pp_cs) + lane : nullptr;
     Pack<T>* out = reinterpret_cast<Pack<T>*>(static_cast<T*>(a.p.out) + ch * a.p.out_cs) + lane;
-    const T* V = static_cast<const T*>(a.op.V);
+    const T* __restrict__ V = static_cast<const T*>(a.op.V);
+    const T* __restrict__ jac = static_cast<const T*>(a.jac);
 
-    // per-column constants
-    const int c0 = ch * CW + lane * W;
-    T sig[W], insc[W], a0s[W], ppc[W];
-    const T* jr[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        const int c = c0 + w;
-        sig[w] = a.p.useSigma ? (T)a.sigma[c] : (T)0;
-        insc[w] = a.p.insc ? (T)a.p.insc[c] : (T)1;
-        a0s[w] = (T)(a.p.a0 * (a.p.xs ? a.p.xs[c] : 1.0));
-        ppc[w] = a.p.ppc ? (T)a.p.ppc[c] : (T)0;
-        jr[w] = JAC ? static_cast<const T*>(a.jac) + (int64_t)a.shift_of[c] * n : nullptr;
-    }
     const T k1 = (T)a.p.k1;
     const T c1 = (T)a.op.c1, c2 = (T)a.op.c2;
     const T dg = (T)(a.p.k1 * a.op.cd + a.p.k0);
@@ -119,12 +120,18 @@ stencil_pass_kernel(KArgs a)
     const int xm2 = (x + N - 2) % N, xp2 = (x + 2) % N;
     const int ym2 = (y + N - 2) % N, yp2 = (y + 2) % N;
     const int64_t NN = (int64_t)N * N;
+    const int64_t cxy = x + (int64_t)N * y;
+    const int64_t oxm1 = xm1 + (int64_t)N * y, oxp1 = xp1 + (int64_t)N * y;
+    const int64_t oym1 = x + (int64_t)N * ym1, oyp1 = x + (int64_t)N * yp1;
+    const int64_t oxm2 = xm2 + (int64_t)N * y, oxp2 = xp2 + (int64_t)N * y;
+    const int64_t oym2 = x + (int64_t)N * ym2, oyp2 = x + (int64_t)N * yp2;
+    const int sbase = lane * W;
 
     auto load = [&](int64_t q) -> Pack<T> {
         Pack<T> v = ldg_pack(in + q * LPP);
         if (JAC) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) v.v[w] *= __ldg(jr[w] + q);
+            for (int w = 0; w < W; ++w) v.v[w] *= __ldg(jac + (int64_t)s_shift[sbase + w] * n + q);
         }
         return v;
     };
@@ -133,62 +140,69 @@ stencil_pass_kernel(KArgs a)
 #pragma unroll
     for (int o = -R; o <= R; ++o) {
         const int zz = ((z0 + o) % N + N) % N;
-        win[o + R] = load(x + (int64_t)N * y + NN * zz);
+        win[o + R] = load(cxy + NN * zz);
     }
 
     for (int z = z0; z < z1; ++z) {
         const int64_t rowz = NN * z;
-        const int64_t p = x + (int64_t)N * y + rowz;
-        Pack<T> s1 = load(xm1 + (int64_t)N * y + rowz);
-        {
-            const Pack<T> t1 = load(xp1 + (int64_t)N * y + rowz);
-            const Pack<T> t2 = load(x + (int64_t)N * ym1 + rowz);
-            const Pack<T> t3 = load(x + (int64_t)N * yp1 + rowz);
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                s1.v[w] += t1.v[w] + t2.v[w] + t3.v[w] + win[R - 1].v[w] + win[R + 1].v[w];
-        }
-        Pack<T> s2;
+        const int64_t p = cxy + rowz;
+        // every load of this plane first: they are independent
+        Pack<T> nb[4 * R];
+        nb[0] = load(oxm1 + rowz);
+        nb[1] = load(oxp1 + rowz);
+        nb[2] = load(oym1 + rowz);
+        nb[3] = load(oyp1 + rowz);
         if (R == 2) {
-            s2 = load(xm2 + (int64_t)N * y + rowz);
-            const Pack<T> t1 = load(xp2 + (int64_t)N * y + rowz);
-            const Pack<T> t2 = load(x + (int64_t)N * ym2 + rowz);
-            const Pack<T> t3 = load(x + (int64_t)N * yp2 + rowz);
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                s2.v[w] += t1.v[w] + t2.v[w] + t3.v[w] + win[0].v[w] + win[2 * R].v[w];
+            nb[4 % (4 * R)] = load(oxm2 + rowz);
+            nb[5 % (4 * R)] = load(oxp2 + rowz);
+            nb[6 % (4 * R)] = load(oym2 + rowz);
+            nb[7 % (4 * R)] = load(oyp2 + rowz);
         }
-        const T vp = a.p.useV ? V[p] : (T)0;
+        const bool more = z + 1 < z1;
+        Pack<T> nxt;
+        if (more) nxt = load(cxy + NN * ((z + 1 + R) % N));
+        Pack<T> tx, tp, tpp;
+        if (xv) tx = ldg_pack(xv + p * LPP);
+        if (pv) tp = ld_pack(pv + p * LPP);
+        if (ppv) tpp = ldg_pack(ppv + p * LPP);
+        const T vp = a.p.useV ? __ldg(V + p) : (T)0;
+        T mp[W];
+        if (JAC) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) mp[w] = __ldg(jac + (int64_t)s_shift[sbase + w] * n + p);
+        }
+        const Pack<T> sig = s_sig[lane], insc = s_insc[lane];
         Pack<T> res;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            T off = c1 * s1.v[w];
-            if (R == 2) off += c2 * s2.v[w];
-            T st = k1 * off + (dg + vp - sig[w]) * win[R].v[w];
-            if (JAC) st *= __ldg(jr[w] + p);
-            res.v[w] = insc[w] * st;
+            T off = c1 * (nb[0].v[w] + nb[1].v[w] + nb[2].v[w] + nb[3].v[w] +
+                          win[R - 1].v[w] + win[R + 1].v[w]);
+            if (R == 2)
+                off += c2 * (nb[4 % (4 * R)].v[w] + nb[5 % (4 * R)].v[w] + nb[6 % (4 * R)].v[w] +
+                             nb[7 % (4 * R)].v[w] + win[0].v[w] + win[2 * R].v[w]);
+            T st = k1 * off + (dg + vp - sig.v[w]) * win[R].v[w];
+            if (JAC) st *= mp[w];
+            res.v[w] = insc.v[w] * st;
         }
         if (xv) {
-            const Pack<T> t = ld_pack(xv + p * LPP);
+            const Pack<T> a0s = s_a0s[lane];
 #pragma unroll
-            for (int w = 0; w < W; ++w) res.v[w] += a0s[w] * t.v[w];
+            for (int w = 0; w < W; ++w) res.v[w] += a0s.v[w] * tx.v[w];
         }
         if (pv) {
-            const Pack<T> t = ld_pack(pv + p * LPP);
 #pragma unroll
-            for (int w = 0; w < W; ++w) res.v[w] -= a2 * t.v[w];
+            for (int w = 0; w < W; ++w) res.v[w] -= a2 * tp.v[w];
         }
         if (ppv) {
-            const Pack<T> t = ld_pack(ppv + p * LPP);
+            const Pack<T> ppc = s_ppc[lane];
 #pragma unroll
-            for (int w = 0; w < W; ++w) res.v[w] -= ppc[w] * t.v[w];
+            for (int w = 0; w < W; ++w) res.v[w] -= ppc.v[w] * tpp.v[w];
         }
         st_pack(out + p * LPP, res);
-        if (z + 1 < z1) {
+        if (more) {
 #pragma unroll
             for (int o = 0; o < 2 * R; ++o) win[o] = win[o + 1];
-            const int zz = (z + 1 + R) % N;
-            win[2 * R] = load(x + (int64_t)N * y + NN * zz);
+            win[2 * R] = nxt;
         }
     }
 }
