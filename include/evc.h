@@ -214,6 +214,43 @@ typedef struct {
  * Synchronises the context's stream.                                          */
 int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
 
+/* Allocation-free batched Gauss quadrature.  The paper has no counterpart.
+ *
+ * For callers that cannot allocate device memory at the point of the call:
+ * code running while another framework is capturing a CUDA graph, code under
+ * a memory pool or budget that forbids new allocations, or runtimes that
+ * have no device allocator of their own.  Nothing here calls cudaMalloc,
+ * cudaFree or any allocating routine; the only device memory used besides
+ * the caller's inputs and outputs is one fixed scratch array compiled into
+ * libevc (3 * EVC_STATIC_QUAD_MAX doubles = 6 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * It computes the same quadrature as the last step of evc_count_slices
+ * (Sec. 3, Eq. gauss_quad): for each column c, ||v||^2 sum over the negative
+ * eigenvalues theta of J_kc of z(1)^2, from coefficients laid out as the
+ * estimator keeps them on the device:
+ *   d_alpha : double[k * ncol],     d_alpha[t*ncol + c] = alpha_{t+1}
+ *   d_beta  : double[(k+1) * ncol], d_beta[t*ncol + c]  = beta_{t+1} (t >= 1 used)
+ *   d_kcol  : int32[ncol] per-column sizes 1 <= kc <= k, or NULL for k
+ *   vnorm2  : ||v||^2 (n for the library's Rademacher probes)
+ *   d_quad  : double[ncol] output
+ * All pointers are device pointers; the call only enqueues one kernel on
+ * `stream` (NULL = legacy default stream) and returns.
+ * Limits: 1 <= k <= EVC_MAX_STEPS, ncol >= 1, k * ncol <= EVC_STATIC_QUAD_MAX;
+ * larger requests return EVC_EINVAL without launching anything, with a
+ * message in errbuf (optional host buffer of errlen bytes).
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current, so make that first
+ * call outside any stream capture.  Every call reuses the same array and the
+ * kernel writes each scratch entry before reading it, so a previous call's
+ * leftovers do not matter; but calls whose kernels can overlap on the GPU
+ * (different streams without ordering between them) race on the array and
+ * give wrong results -- serialise them.                                       */
+#define EVC_STATIC_QUAD_MAX 262144
+int evc_gauss_quadrature_static(const double* d_alpha, const double* d_beta, const int* d_kcol,
+                                int k, int ncol, double vnorm2, double* d_quad, void* stream,
+                                char* errbuf, size_t errlen);
+
 const char* evc_last_error(const evc_ctx* ctx);
 void evc_destroy(evc_ctx* ctx);
 /* Library version, major*10000 + minor*100 + patch.                           */

@@ -36,7 +36,8 @@ EXPORTED = [
     "evc_create_csr", "evc_create_stencil", "evc_set_values", "evc_set_precond",
     "evc_workspace_bytes", "evc_set_workspace", "evc_count", "evc_count_slices",
     "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_set_option",
-    "evc_get_profile", "evc_last_error", "evc_destroy", "evc_version",
+    "evc_get_profile", "evc_gauss_quadrature_static", "evc_last_error", "evc_destroy",
+    "evc_version",
 ]
 
 
@@ -88,6 +89,8 @@ def load(path: str | None = None):
             "evc_get_tridiag": (i32, [vp, dp, dp, ip]),
             "evc_set_option": (i32, [vp, i32, i64]),
             "evc_get_profile": (i32, [vp, C.POINTER(evc_prof_rec), i32, ip]),
+            "evc_gauss_quadrature_static": (i32, [vp, vp, vp, i32, i32, d, vp, vp, C.c_char_p,
+                                                  C.c_size_t]),
             "evc_last_error": (C.c_char_p, [vp]),
             "evc_destroy": (None, [vp]),
             "evc_version": (i32, []),
@@ -222,6 +225,17 @@ def evc_get_profile(ctx):
     recs = (evc_prof_rec * max(1, n.value))()
     _check(ctx, lib.evc_get_profile(ctx, recs, n.value, C.byref(n)))
     return [(r.kind, r.step, r.ms, r.bytes) for r in recs[:n.value]]
+
+
+EVC_STATIC_QUAD_MAX = 262144
+
+
+def evc_gauss_quadrature_static(d_alpha, d_beta, d_kcol, k, ncol, vnorm2, d_quad, stream=None):
+    """Allocation-free quadrature (device pointers in and out); returns (status, message)."""
+    buf = C.create_string_buffer(256)
+    rc = load().evc_gauss_quadrature_static(d_alpha, d_beta, d_kcol, int(k), int(ncol),
+                                            float(vnorm2), d_quad, stream, buf, 256)
+    return rc, buf.value.decode()
 
 
 def evc_last_error(ctx):
