@@ -193,7 +193,7 @@ enum {
     EVC_K_STENCIL = 2,   /* one stencil pass (Chebyshev step / H apply)       */
     EVC_K_CSR = 3,       /* CSR operator apply                                */
     EVC_K_DOTS = 4,      /* reorthogonalisation dot products                  */
-    EVC_K_REDUCE = 5,    /* dot-product reduction, alpha                      */
+    EVC_K_REDUCE = 5,    /* dot-product reduction, alpha, coefficients        */
     EVC_K_UPDATE = 6,    /* reorthogonalisation update and norm               */
     EVC_K_FINISH = 7     /* beta, eigensolve, quadrature, stop rule           */
 };

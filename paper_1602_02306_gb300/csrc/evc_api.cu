@@ -118,8 +118,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int choose_nblk(int64_t n, int nchunk)
 {
-    // about 4 resident blocks per SM on 152 SMs; at least 64 rows per block
-    const int64_t target = (4 * 152 + nchunk - 1) / nchunk;
+    // two resident blocks per SM of the streaming reorthogonalisation kernels
+    // on 152 SMs; at least 64 rows per block
+    const int64_t target = (2 * 152 + nchunk - 1) / nchunk;
     const int64_t maxb = std::max<int64_t>(1, (n + 63) / 64);
     return (int)std::max<int64_t>(1, std::min(target, maxb));
 }
@@ -182,6 +183,7 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.steps = I(S);
     r.sdone = I(S);
     r.chunk_active = I(nchunk);
+    r.cnt_upd = I(nchunk);
     r.part_dot = D((size_t)nchunk * nblk * kmax * CW);
     r.part_gram = D((size_t)nchunk * nblk * kmax * CW);
     r.hbuf = D((size_t)kmax * ncol);
@@ -517,10 +519,10 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         if (!rc)
             rc = rec(ctx, EVC_K_UPDATE, i, vec * (i + 2), [&] { return launch_update<T>(r, i, st); });
         const bool last = (i == r.kmax);
-        if (!rc)
-            rc = rec(ctx, EVC_K_FINISH, i, (double)r.nchunk * r.nblk * CW * 8 + colb * 8,
-                     [&] { return launch_finish(r, i, adaptive || last, last, st); });
-        if (!rc) rc = rec(ctx, EVC_K_FINISH, i, colb, [&] { return launch_active(r, st); });
+        if (!rc && (adaptive || last))
+            rc = rec(ctx, EVC_K_FINISH, i, colb * (2.0 * i + 2),
+                     [&] { return launch_finish(r, i, true, last, st); });
+        if (!rc && adaptive) rc = rec(ctx, EVC_K_FINISH, i, colb, [&] { return launch_active(r, st); });
     }
     return rc;
 }
@@ -672,6 +674,10 @@ int check_device_error(evc_ctx* ctx)
     CU(cudaStreamSynchronize(ctx->stream));
     if (herr == DERR_NUMERIC)
         return fail(ctx, EVC_ENUMERIC, "non-finite alpha/beta or tridiagonal eigensolver failure");
+    if (herr == DERR_TIMEOUT)
+        return fail(ctx, EVC_ETIMEOUT, "a bounded device wait gave up (results are invalid)");
+    if (herr == DERR_BOUNDS)
+        return fail(ctx, EVC_ECUDA, "a bulk copy failed its bounds/alignment check (results are invalid)");
     if (herr) return fail(ctx, EVC_ECUDA, "device error flag %d", herr);
     return EVC_OK;
 }

@@ -23,7 +23,7 @@ constexpr int kMaxSteps = 256;         // == EVC_MAX_STEPS
 constexpr int kThreads = 256;          // threads per block of the streaming kernels
 
 // Device-side error codes (mirror evc_status).
-enum { DERR_NONE = 0, DERR_NUMERIC = 4 };
+enum { DERR_NONE = 0, DERR_NUMERIC = 4, DERR_TIMEOUT = 5, DERR_BOUNDS = 7 };
 
 // One run (a call of evc_count_slices) -- device pointers and sizes.
 struct Run {
@@ -55,6 +55,7 @@ struct Run {
     int* steps;              // [S]
     int* sdone;              // [S]
     int* chunk_active;       // [nchunk]
+    int* cnt_upd;            // [nchunk]  blocks done, update kernel (last block forms beta)
     int* err;                // [1]
     double* part_dot;        // [nchunk][nblk][kmax][CW]  partial P_j . w
     double* part_gram;       // [nchunk][nblk][kmax][CW]  partial P_j . P_{i-1}
@@ -115,10 +116,10 @@ cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V
                                  double eps, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st);
-cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
-cudaError_t launch_coef(const Run& r, int i, cudaStream_t st);
 template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st);
+cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
+cudaError_t launch_coef(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_finish(const Run& r, int i, bool do_quad, bool last, cudaStream_t st);
 cudaError_t launch_active(const Run& r, cudaStream_t st);
 

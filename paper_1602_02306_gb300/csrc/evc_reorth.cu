@@ -5,11 +5,13 @@
 // Per step i, for every column c (w = C q_i - beta_i q_{i-1} is in slot i):
 //   dots    h_j = q_j^T w and G_ij = q_j^T q_i, j = 1..i, in one sweep over
 //           the basis (partials per row block)
-//   reduce  h, the new Gram row, alpha_i = h_i       (FP64, fixed order)
-//   coef    c = h + (I - G) h                        (FP64, per column)
-//   update  w <- w - Q_i c;  ||w||^2 partials
-//   finish  beta_{i+1} = ||w||, s_{i+1} = 1/beta_{i+1}, breakdown test,
-//           eig(J_i) -> quadrature, per-shift mean L(i) and stop rule.
+//   reduce  sums the partials (FP64, fixed order): h, the new Gram row,
+//           alpha_i = h_i
+//   coef    c = h + (I - G) h
+//   update  w <- w - Q_i c;  ||w||^2 partials; its last block per chunk sets
+//           beta_{i+1} = ||w||, s_{i+1} = 1/beta_{i+1} and the breakdown test
+//   finish  eig(J_i) -> quadrature, per-shift mean L(i) and stop rule
+//           (every step under a tolerance, else once after the last step).
 // In exact arithmetic G = I, c = h, and the single fused classical
 // Gram-Schmidt sweep equals Algorithm 1's "alpha_i = q_i^T w;
 // w -= alpha_i q_i; w -= Q_i (Q_i^T w)" (the second projection's i-th
@@ -26,6 +28,7 @@
 // result does not depend on which other columns share the launch.
 #include "evc_internal.cuh"
 #include "evc_tridiag.cuh"
+#include "evc_bulk.cuh"
 
 #include <cmath>
 
@@ -33,7 +36,6 @@ namespace evc {
 namespace {
 
 constexpr int JB = 8;          // basis vectors per pass of the dot kernel
-constexpr int RUN = 16;        // rows per FP32 partial-sum run
 constexpr int WARPS = kThreads / 32;
 static_assert(JB == WARPS, "the dot kernel's warp tree maps warp q to basis vector jg + q");
 
@@ -82,7 +84,10 @@ __global__ void init_state_kernel(Run r)
         r.Lfinal[t] = 0.0;
         r.steps[t] = 0;
     }
-    if (t < r.nchunk) r.chunk_active[t] = 1;
+    if (t < r.nchunk) {
+        r.chunk_active[t] = 1;
+        r.cnt_upd[t] = 0;
+    }
     if (t == 0) *r.err = DERR_NONE;
 }
 
@@ -101,6 +106,26 @@ __global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, doubl
     }
 }
 
+// Bulk copy with its preconditions checked first: a 16-byte aligned source
+// inside [lo, hi), a 16-byte aligned destination, a size that is a positive
+// multiple of 16.  A violation records DERR_BOUNDS and skips the copy (the
+// waiting consumers then give up through their bounded waits).
+__device__ __forceinline__ bool checked_bulk(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar, const void* lo, const void* hi,
+                                             int* err)
+{
+    const char* s = static_cast<const char*>(src);
+    const bool ok = bytes > 0 && (bytes & 15) == 0 && ((uintptr_t)src & 15) == 0 &&
+                    ((uintptr_t)smem_addr(dst) & 15) == 0 && s >= static_cast<const char*>(lo) &&
+                    s + bytes <= static_cast<const char*>(hi);
+    if (!ok) {
+        atomicExch(err, DERR_BOUNDS);
+        return false;
+    }
+    bulk_g2s(dst, src, bytes, bar);
+    return true;
+}
+
 template <typename T> struct Acc { typedef float run; };
 template <> struct Acc<double> { typedef double run; };
 
@@ -111,83 +136,152 @@ __device__ __forceinline__ void row_range(int64_t n, int nblk, int blk, int64_t&
     r1 = min(n, r0 + per);
 }
 
+// Streaming layout of the two reorthogonalisation kernels.  Each block owns
+// a contiguous row range of one chunk and walks it in row tiles.  One
+// producer warp issues asynchronous bulk copies (cp.async.bulk, mbarrier
+// completion) of every basis tile P_j[tile] into a ring of shared-memory
+// stages, so the bytes in flight are set by shared memory, not registers;
+// eight consumer warps compute from shared memory and release the stages.
+constexpr int CWARPS = 8;                       // consumer warps
+constexpr int BTHREADS = (CWARPS + 1) * 32;     // + one producer warp
+constexpr int DSTAGE = 4096;                    // bytes per stage, dot kernel
+constexpr int NSW = 2;                          // stages per consumer warp, dot kernel
+constexpr int DNS = CWARPS * NSW;               // stages, dot kernel
+constexpr int USTAGE = 8192;                    // bytes per stage, update kernel
+constexpr int UNS = 10;                         // stages, update kernel
+
 // part_dot[ch][blk][j][lane]  = sum_{rows of blk} P_j[row][lane] * w[row][lane]
 // part_gram[ch][blk][j][lane] = sum_{rows of blk} P_j[row][lane] * P_{i-1}[row][lane]
-// for j < i.  The block walks its rows in slabs of WARPS*RTD rows; each warp
-// holds RTD-row tiles of w and of P_{i-1} in registers and streams JB basis
-// tiles at a time against both (independent loads).  Tile sums (FP32 runs of
-// RTD rows in mixed mode) go through a fixed shared-memory tree into per-block
-// FP64 accumulators, so the summation order is fixed and w is read once.
-constexpr int RT = 16;          // rows per warp tile (update)
-constexpr int RTD = 8;          // rows per warp tile (dots)
-
+// for j < i.  Consumer warp q handles the basis vectors j = q, q+8, ...: it
+// holds the w and P_{i-1} tiles of the current row tile in registers and
+// owns the FP64 accumulators of its j's in shared memory, so every sum has a
+// fixed order (tiles in row order, FP32 runs of one tile in mixed mode).
+// Each consumer warp has its own ring of NSW stages, so the item a warp
+// waits for is always one phase ahead of the previous item in that stage,
+// which the same warp consumed (mbarrier parities cannot alias).
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(BTHREADS)
 reorth_dots_kernel(Run r, int i)
 {
+    constexpr int TR = DSTAGE / (CW * (int)sizeof(T));   // rows per tile
     const int ch = blockIdx.y, blk = blockIdx.x;
     if (!r.chunk_active[ch]) return;
-    extern __shared__ double sm[];
-    double* bacc = sm;                              // [i][CW]
-    double* bgram = sm + (size_t)i * CW;            // [i][CW]
-    double* red = sm + (size_t)2 * i * CW;          // [WARPS][2*JB][CW]
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* stage = reinterpret_cast<T*>(smem);                               // [DNS][TR*CW]
+    T* wq = reinterpret_cast<T*>(smem + (size_t)DNS * DSTAGE);           // [2][2][TR*CW]
+    double* acc = reinterpret_cast<double*>(smem + (size_t)(DNS + 4) * DSTAGE);   // [2][i][CW]
+    uint64_t* full = reinterpret_cast<uint64_t*>(acc + (size_t)2 * i * CW);
+    uint64_t* empty = full + DNS;
+    uint64_t* wqfull = empty + DNS;
+    uint64_t* wqempty = wqfull + 2;
+    __shared__ int s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < 2 * i * CW; e += blockDim.x) sm[e] = 0.0;
     int64_t r0, r1;
     row_range(r.n, r.nblk, blk, r0, r1);
-    const T* __restrict__ P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
-    const T* __restrict__ w = P + (int64_t)i * r.slot_stride;
-    const T* __restrict__ q = P + (int64_t)(i - 1) * r.slot_stride;
+    const int ntile = r1 > r0 ? (int)((r1 - r0 + TR - 1) / TR) : 0;
+    const T* P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
+    const T* w = P + (int64_t)i * r.slot_stride;
+    const T* q = P + (int64_t)(i - 1) * r.slot_stride;
+    const void* lo = P;                                  // this chunk's basis
+    const void* hi = P + r.chunk_stride;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < DNS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&wqfull[b], 1);
+            mbar_init(&wqempty[b], CWARPS);
+        }
+        mbar_init_fence();
+        s_fail = 0;
+    }
+    for (int e = threadIdx.x; e < 2 * i * CW; e += blockDim.x) acc[e] = 0.0;
+    __syncthreads();
     typedef typename Acc<T>::run RTy;
-    for (int64_t base = r0; base < r1; base += (int64_t)WARPS * RTD) {
-        const int64_t t0 = base + (int64_t)warp * RTD;
-        T wv[RTD], qv[RTD];
-#pragma unroll
-        for (int t = 0; t < RTD; ++t) {
-            const bool ok = t0 + t < r1;
-            wv[t] = ok ? __ldg(w + (t0 + t) * CW + lane) : (T)0;
-            qv[t] = ok ? __ldg(q + (t0 + t) * CW + lane) : (T)0;
-        }
-        for (int jg = 0; jg < i; jg += JB) {
-            RTy a[JB], b[JB];
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) { a[jj] = 0; b[jj] = 0; }
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) {
-                if (jg + jj < i) {
-                    const T* __restrict__ Pj = P + (int64_t)(jg + jj) * r.slot_stride + t0 * CW + lane;
-#pragma unroll
-                    for (int t = 0; t < RTD; ++t)
-                        if (t0 + t < r1) {
-                            const RTy pj = (RTy)__ldg(Pj + t * CW);
-                            a[jj] += pj * (RTy)wv[t];
-                            b[jj] += pj * (RTy)qv[t];
-                        }
+    bool ok = true;
+    if (warp == CWARPS) {
+        if (lane == 0) {
+            int64_t lastk[DNS];                  // last item issued into each stage
+            int lastt[2] = {-1, -1};             // last tile issued into each w/q buffer
+            for (int s = 0; s < DNS; ++s) lastk[s] = -1;
+            for (int t = 0; t < ntile && ok; ++t) {
+                const int64_t row0 = r0 + (int64_t)t * TR;
+                const uint32_t bytes = (uint32_t)(min((int64_t)TR, r1 - row0) * CW * sizeof(T));
+                const int b = t & 1;
+                if (t >= 2 && !(ok = mbar_wait(&wqempty[b], ((t >> 1) - 1) & 1))) break;
+                lastt[b] = t;
+                mbar_arrive_expect_tx(&wqfull[b], 2 * bytes);
+                ok = checked_bulk(wq + (size_t)(2 * b) * TR * CW, w + row0 * CW, bytes, &wqfull[b],
+                                  lo, hi, r.err) &&
+                     checked_bulk(wq + (size_t)(2 * b + 1) * TR * CW, q + row0 * CW, bytes,
+                                  &wqfull[b], lo, hi, r.err);
+                for (int j = 0; j < i && ok; ++j) {
+                    // k-th item of consumer warp cw lives in stage cw*NSW + k % NSW
+                    const int cw = j % CWARPS;
+                    const int64_t k = (int64_t)t * ((i - cw + CWARPS - 1) / CWARPS) + j / CWARPS;
+                    const int s = cw * NSW + (int)(k % NSW);
+                    if (k >= NSW && !(ok = mbar_wait(&empty[s], ((k / NSW) - 1) & 1))) break;
+                    lastk[s] = k;
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    ok = checked_bulk(stage + (size_t)s * TR * CW,
+                                      P + (int64_t)j * r.slot_stride + row0 * CW, bytes, &full[s],
+                                      lo, hi, r.err);
                 }
             }
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) {
-                red[((size_t)warp * 2 * JB + jj) * CW + lane] = (double)a[jj];
-                red[((size_t)warp * 2 * JB + JB + jj) * CW + lane] = (double)b[jj];
+            if (!ok) {
+                // let the copies already issued land before the block exits
+                for (int s = 0; s < DNS; ++s)
+                    if (lastk[s] >= 0) mbar_wait(&full[s], (lastk[s] / NSW) & 1);
+                for (int b = 0; b < 2; ++b)
+                    if (lastt[b] >= 0) mbar_wait(&wqfull[b], (lastt[b] >> 1) & 1);
             }
-            __syncthreads();
-            if (jg + warp < i) {
-                double sa = 0.0, sb = 0.0;
-#pragma unroll
-                for (int qq = 0; qq < WARPS; ++qq) {
-                    sa += red[((size_t)qq * 2 * JB + warp) * CW + lane];
-                    sb += red[((size_t)qq * 2 * JB + JB + warp) * CW + lane];
-                }
-                bacc[(size_t)(jg + warp) * CW + lane] += sa;
-                bgram[(size_t)(jg + warp) * CW + lane] += sb;
-            }
-            __syncthreads();
         }
+    } else {
+        for (int t = 0; t < ntile && ok; ++t) {
+            const int64_t row0 = r0 + (int64_t)t * TR;
+            const int rows = (int)min((int64_t)TR, r1 - row0);
+            const int b = t & 1;
+            if (!(ok = mbar_wait(&wqfull[b], (t >> 1) & 1))) break;
+            T wv[TR], qv[TR];
+#pragma unroll
+            for (int rr = 0; rr < TR; ++rr) {
+                wv[rr] = rr < rows ? wq[(size_t)(2 * b) * TR * CW + rr * CW + lane] : (T)0;
+                qv[rr] = rr < rows ? wq[(size_t)(2 * b + 1) * TR * CW + rr * CW + lane] : (T)0;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&wqempty[b]);
+            const int per = (i - warp + CWARPS - 1) / CWARPS;   // my items per tile
+            for (int j = warp; j < i; j += CWARPS) {
+                const int64_t k = (int64_t)t * per + j / CWARPS;
+                const int s = warp * NSW + (int)(k % NSW);
+                if (!(ok = mbar_wait(&full[s], (k / NSW) & 1))) break;
+                const T* st = stage + (size_t)s * TR * CW + lane;
+                RTy a = 0, g = 0;
+#pragma unroll
+                for (int rr = 0; rr < TR; ++rr) {
+                    // rows past the tail of a short tile hold stale shared memory
+                    const RTy pv = rr < rows ? (RTy)st[rr * CW] : (RTy)0;
+                    a += pv * (RTy)wv[rr];
+                    g += pv * (RTy)qv[rr];
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                acc[(size_t)j * CW + lane] += (double)a;
+                acc[(size_t)(i + j) * CW + lane] += (double)g;
+            }
+        }
+    }
+    if (!ok) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) atomicCAS(r.err, DERR_NONE, DERR_TIMEOUT);
+        return;
     }
     for (int e = threadIdx.x; e < i * CW; e += blockDim.x) {
         const int64_t o = (((int64_t)ch * r.nblk + blk) * r.kmax + e / CW) * CW + (e % CW);
-        r.part_dot[o] = bacc[e];
-        r.part_gram[o] = bgram[e];
+        r.part_dot[o] = acc[e];
+        r.part_gram[o] = acc[(size_t)i * CW + e];
     }
 }
 
@@ -197,134 +291,224 @@ __device__ __forceinline__ int64_t tri(int a, int b)
     return (int64_t)a * (a + 1) / 2 + b;
 }
 
-// h_j = s_j * sum_blk part_dot;  G_{i-1,j} = s_{i-1} s_j * sum_blk part_gram;
-// alpha_i = h_{i-1}  (slot j holds q_{j+1})
-__global__ void reorth_reduce_kernel(Run r, int i)
+// h_j = s_j sum_b part_dot[ch][b][j][:], G_{i-1,j} = s_{i-1} s_j sum_b part_gram,
+// alpha_i = h_{i-1}.  One block of RW warps per (chunk, j): warp q sums the row
+// blocks b = q, q+RW, ... for the 32 columns (one coalesced 256-byte load per
+// b), then the warps' sums are added in warp order (fixed summation order).
+constexpr int RW = 4;
+__global__ void __launch_bounds__(RW * 32)
+reorth_reduce_kernel(Run r, int i)
+{
+    const int ch = blockIdx.x % r.nchunk, j = blockIdx.x / r.nchunk;
+    if (!r.chunk_active[ch]) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double sh[RW][CW], sg[RW][CW];
+    double ah = 0.0, ag = 0.0;
+#pragma unroll 4
+    for (int b = warp; b < r.nblk; b += RW) {
+        const int64_t o = (((int64_t)ch * r.nblk + b) * r.kmax + j) * CW + lane;
+        ah += r.part_dot[o];
+        ag += r.part_gram[o];
+    }
+    sh[warp][lane] = ah;
+    sg[warp][lane] = ag;
+    __syncthreads();
+    if (warp == 0) {
+        double th = 0.0, tg = 0.0;
+#pragma unroll
+        for (int q = 0; q < RW; ++q) { th += sh[q][lane]; tg += sg[q][lane]; }
+        const int c = ch * CW + lane;
+        const double sj = r.scl[(int64_t)j * r.ncol + c];
+        const double si = r.scl[(int64_t)(i - 1) * r.ncol + c];
+        const double h = th * sj;                    // q_j . w
+        r.hbuf[(int64_t)j * r.ncol + c] = h;
+        r.gram[tri(i - 1, j) * r.ncol + c] = tg * sj * si;   // q_j . q_i
+        if (j == i - 1) r.alpha[(int64_t)(i - 1) * r.ncol + c] = h;
+    }
+}
+
+// c = h + (I - G) h;  g_j = c_j s_j multiplies the unnormalised P_j.
+// One thread per (column, j).
+__global__ void reorth_coef_kernel(Run r, int i)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= r.ncol * i) return;
     const int c = t % r.ncol, j = t / r.ncol;
-    const int ch = c / CW, lane = c % CW;
-    if (!r.chunk_active[ch]) return;
-    double sh = 0.0, sg = 0.0;
-    for (int b = 0; b < r.nblk; ++b) {
-        const int64_t o = (((int64_t)ch * r.nblk + b) * r.kmax + j) * CW + lane;
-        sh += r.part_dot[o];
-        sg += r.part_gram[o];
-    }
-    const double sj = r.scl[(int64_t)j * r.ncol + c];
-    const double si = r.scl[(int64_t)(i - 1) * r.ncol + c];
-    const double h = sh * sj;
-    r.hbuf[(int64_t)j * r.ncol + c] = h;
-    r.gram[tri(i - 1, j) * r.ncol + c] = sg * sj * si;
-    if (j == i - 1) r.alpha[(int64_t)(i - 1) * r.ncol + c] = h;
-}
-
-// c = h + (I - G) h, g_j = c_j s_j (coefficients of the unnormalised P_j)
-__global__ void reorth_coef_kernel(Run r, int i)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= r.ncol) return;
     if (!r.chunk_active[c / CW]) return;
-    for (int j = 0; j < i; ++j) {
-        double gh = 0.0;
-        for (int l = 0; l < i; ++l) {
-            const double G = r.gram[(j >= l ? tri(j, l) : tri(l, j)) * r.ncol + c];
-            gh += G * r.hbuf[(int64_t)l * r.ncol + c];
-        }
-        const double hj = r.hbuf[(int64_t)j * r.ncol + c];
-        r.g[(int64_t)j * r.ncol + c] = (2.0 * hj - gh) * r.scl[(int64_t)j * r.ncol + c];
+    double gh = 0.0;
+#pragma unroll 4
+    for (int l = 0; l < i; ++l) {
+        const double G = r.gram[(j >= l ? tri(j, l) : tri(l, j)) * r.ncol + c];
+        gh += G * r.hbuf[(int64_t)l * r.ncol + c];
     }
+    const double hj = r.hbuf[(int64_t)j * r.ncol + c];
+    r.g[(int64_t)j * r.ncol + c] = (2.0 * hj - gh) * r.scl[(int64_t)j * r.ncol + c];
 }
 
 // w <- w - sum_{j<i} g_j P_j (in place, slot i); part_nrm = partial ||w||^2.
-// Same warp tiling as the dot kernel: the w tile lives in registers while
-// every P_j tile streams past it.
+// The producer streams, per row tile, the w tile and then every P_j tile;
+// consumer warp q owns rows q*RPW.. of the tile in registers and applies
+// every P_j stage to them, then writes the tile back.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(BTHREADS)
 reorth_update_kernel(Run r, int i)
 {
+    constexpr int TR = USTAGE / (CW * (int)sizeof(T));   // rows per tile
+    constexpr int RPW = TR / CWARPS;                      // rows per consumer warp
     const int ch = blockIdx.y, blk = blockIdx.x;
     if (!r.chunk_active[ch]) return;
-    extern __shared__ unsigned char smem_raw[];
-    T* gs = reinterpret_cast<T*>(smem_raw);            // [i][CW]
-    __shared__ double red[WARPS][CW];
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* stage = reinterpret_cast<T*>(smem);                                // [UNS][TR*CW]
+    T* wbuf = reinterpret_cast<T*>(smem + (size_t)UNS * USTAGE);          // [2][TR*CW]
+    T* gs = reinterpret_cast<T*>(smem + (size_t)(UNS + 2) * USTAGE);      // [i][CW]
+    uint64_t* full = reinterpret_cast<uint64_t*>(
+        smem + (size_t)(UNS + 2) * USTAGE + (((size_t)i * CW * sizeof(T) + 15) & ~(size_t)15));
+    uint64_t* empty = full + UNS;
+    uint64_t* wfull = empty + UNS;
+    uint64_t* wempty = wfull + 2;
+    __shared__ double red[CWARPS + 1][CW];
+    __shared__ int s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < i * CW; e += blockDim.x)
         gs[e] = (T)r.g[(int64_t)(e / CW) * r.ncol + ch * CW + (e % CW)];
-    __syncthreads();
     int64_t r0, r1;
     row_range(r.n, r.nblk, blk, r0, r1);
-    const T* __restrict__ P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
-    T* __restrict__ w = static_cast<T*>(r.basis) + ch * r.chunk_stride + (int64_t)i * r.slot_stride;
-    typedef typename Acc<T>::run RTy;
-    double acc = 0.0;
-    for (int64_t t0 = r0 + (int64_t)warp * RT; t0 < r1; t0 += (int64_t)WARPS * RT) {
-        T wv[RT];
-#pragma unroll
-        for (int t = 0; t < RT; ++t) wv[t] = (t0 + t < r1) ? w[(t0 + t) * CW + lane] : (T)0;
-#pragma unroll 2
-        for (int j = 0; j < i; ++j) {
-            const T gj = gs[j * CW + lane];
-            const T* __restrict__ Pj = P + (int64_t)j * r.slot_stride + t0 * CW + lane;
-#pragma unroll
-            for (int t = 0; t < RT; ++t)
-                if (t0 + t < r1) wv[t] -= gj * __ldg(Pj + t * CW);
+    const int ntile = r1 > r0 ? (int)((r1 - r0 + TR - 1) / TR) : 0;
+    const T* P = static_cast<const T*>(r.basis) + ch * r.chunk_stride;
+    T* w = static_cast<T*>(r.basis) + ch * r.chunk_stride + (int64_t)i * r.slot_stride;
+    const void* lo = P;
+    const void* hi = P + r.chunk_stride;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < UNS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CWARPS);
         }
-        RTy nr = 0;
-#pragma unroll
-        for (int t = 0; t < RT; ++t)
-            if (t0 + t < r1) {
-                w[(t0 + t) * CW + lane] = wv[t];
-                nr += (RTy)wv[t] * (RTy)wv[t];
-            }
-        acc += (double)nr;
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&wfull[b], 1);
+            mbar_init(&wempty[b], CWARPS);
+        }
+        mbar_init_fence();
+        s_fail = 0;
     }
+    __syncthreads();
+    typedef typename Acc<T>::run RTy;
+    bool ok = true;
+    double acc = 0.0;
+    if (warp == CWARPS) {
+        if (lane == 0) {
+            int64_t item = 0;
+            int64_t lastk[UNS];
+            int lastt[2] = {-1, -1};
+            for (int s = 0; s < UNS; ++s) lastk[s] = -1;
+            for (int t = 0; t < ntile && ok; ++t) {
+                const int64_t row0 = r0 + (int64_t)t * TR;
+                const uint32_t bytes = (uint32_t)(min((int64_t)TR, r1 - row0) * CW * sizeof(T));
+                const int b = t & 1;
+                if (t >= 2 && !(ok = mbar_wait(&wempty[b], ((t >> 1) - 1) & 1))) break;
+                lastt[b] = t;
+                mbar_arrive_expect_tx(&wfull[b], bytes);
+                ok = checked_bulk(wbuf + (size_t)b * TR * CW, w + row0 * CW, bytes, &wfull[b], lo, hi,
+                                  r.err);
+                for (int j = 0; j < i && ok; ++j, ++item) {
+                    const int s = (int)(item % UNS);
+                    if (item >= UNS && !(ok = mbar_wait(&empty[s], ((item / UNS) - 1) & 1))) break;
+                    lastk[s] = item;
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    ok = checked_bulk(stage + (size_t)s * TR * CW,
+                                      P + (int64_t)j * r.slot_stride + row0 * CW, bytes, &full[s],
+                                      lo, hi, r.err);
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the block exits
+                for (int s = 0; s < UNS; ++s)
+                    if (lastk[s] >= 0) mbar_wait(&full[s], (lastk[s] / UNS) & 1);
+                for (int b = 0; b < 2; ++b)
+                    if (lastt[b] >= 0) mbar_wait(&wfull[b], (lastt[b] >> 1) & 1);
+            }
+        }
+    } else {
+        int64_t item = 0;
+        for (int t = 0; t < ntile && ok; ++t) {
+            const int64_t row0 = r0 + (int64_t)t * TR;
+            const int rows = (int)min((int64_t)TR, r1 - row0);
+            const int b = t & 1;
+            if (!(ok = mbar_wait(&wfull[b], (t >> 1) & 1))) break;
+            T wv[RPW];
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) {
+                const int row = warp * RPW + rr;
+                wv[rr] = row < rows ? wbuf[(size_t)b * TR * CW + row * CW + lane] : (T)0;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&wempty[b]);
+            for (int j = 0; j < i; ++j, ++item) {
+                const int s = (int)(item % UNS);
+                if (!(ok = mbar_wait(&full[s], (item / UNS) & 1))) break;
+                const T gj = gs[j * CW + lane];
+                const T* st = stage + (size_t)s * TR * CW + (size_t)warp * RPW * CW + lane;
+#pragma unroll
+                for (int rr = 0; rr < RPW; ++rr)
+                    if (warp * RPW + rr < rows) wv[rr] -= gj * st[rr * CW];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            if (!ok) break;
+            RTy nr = 0;
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) {
+                const int row = warp * RPW + rr;
+                if (row < rows) {
+                    w[(row0 + row) * CW + lane] = wv[rr];
+                    nr += (RTy)wv[rr] * (RTy)wv[rr];
+                }
+            }
+            acc += (double)nr;
+        }
+    }
+    if (!ok) s_fail = 1;
     red[warp][lane] = acc;
     __syncthreads();
-    if (warp == 0) {
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < WARPS; ++q) s += red[q][lane];
-        r.part_nrm[((int64_t)ch * r.nblk + blk) * CW + lane] = s;
+    if (s_fail) {
+        if (threadIdx.x == 0) atomicCAS(r.err, DERR_NONE, DERR_TIMEOUT);
+        return;
     }
-}
-
-// Gauss quadrature of column c's J_k; eigensolver scratch in the workspace,
-// [3][kmax][ncol] (coalesced across columns).
-__device__ double gauss_quadrature(const Run& r, int c, int k, double vnorm2)
-{
-    const int64_t plane = (int64_t)r.kmax * r.ncol;
-    return tridiag_gauss_quadrature(r.alpha + c, r.beta + c, r.ncol, k, vnorm2, r.eigw + c,
-                                    r.eigw + plane + c, r.eigw + 2 * plane + c, r.ncol);
-}
-
-// One block per shift (block S handles the padding columns).
-__global__ void __launch_bounds__(kThreads)
-finish_kernel(Run r, int i, int do_quad, int last)
-{
-    const int s = blockIdx.x;
-    const bool real = s < r.S;
-    if (real && r.sdone[s]) return;
-    const int cbeg = real ? s * r.m : r.ncol_real;
-    const int cend = real ? cbeg + r.m : r.ncol;
-    __shared__ double red[kThreads];
-    __shared__ int stop;
-    double lsum = 0.0;
-    for (int c = cbeg + threadIdx.x; c < cend; c += blockDim.x) {
-        const int ch = c / CW, lane = c % CW;
+    if (warp == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int qq = 0; qq < CWARPS; ++qq) sum += red[qq][lane];
+        r.part_nrm[((int64_t)ch * r.nblk + blk) * CW + lane] = sum;
+    }
+    // The last block of this chunk forms beta_{i+1}, the new scale s_i and the
+    // breakdown test for the chunk's columns (no extra launch).
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&r.cnt_upd[ch], 1) == r.nblk - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    {
+        double ps = 0.0;
+        for (int b = warp; b < r.nblk; b += CWARPS + 1)
+            ps += r.part_nrm[((int64_t)ch * r.nblk + b) * CW + lane];
+        red[warp][lane] = ps;
+    }
+    __syncthreads();
+    if (threadIdx.x < CW) {
+        const int ln = threadIdx.x, c = ch * CW + ln;
         if (r.kdone[c] == 0) {
             double nrm2 = 0.0;
-            for (int b = 0; b < r.nblk; ++b)
-                nrm2 += r.part_nrm[((int64_t)ch * r.nblk + b) * CW + lane];
+#pragma unroll
+            for (int q = 0; q < CWARPS + 1; ++q) nrm2 += red[q][ln];
             const double beta = sqrt(nrm2);
             const double al = r.alpha[(int64_t)(i - 1) * r.ncol + c];
             const double bprev = r.beta[(int64_t)(i - 1) * r.ncol + c];
-            double sc = fmax(r.colscale[c], fmax(fabs(al), bprev));
+            const double sc = fmax(r.colscale[c], fmax(fabs(al), bprev));
             r.colscale[c] = sc;
             r.beta[(int64_t)i * r.ncol + c] = beta;
             if (!isfinite(beta) || !isfinite(al)) {
-                if (real) atomicExch(r.err, DERR_NUMERIC);
+                if (c < r.ncol_real) atomicExch(r.err, DERR_NUMERIC);
                 r.kdone[c] = i;
                 r.scl[(int64_t)i * r.ncol + c] = 0.0;
                 r.ppc[c] = 0.0;
@@ -338,7 +522,35 @@ finish_kernel(Run r, int i, int do_quad, int last)
                 r.ppc[c] = beta * r.scl[(int64_t)(i - 1) * r.ncol + c];
             }
         }
-        if (do_quad && real) {
+    }
+    if (threadIdx.x == 0) r.cnt_upd[ch] = 0;
+}
+
+// Gauss quadrature of column c's J_k; eigensolver scratch in the workspace,
+// [3][kmax][ncol] (coalesced across columns).
+__device__ double gauss_quadrature(const Run& r, int c, int k, double vnorm2)
+{
+    const int64_t plane = (int64_t)r.kmax * r.ncol;
+    return tridiag_gauss_quadrature(r.alpha + c, r.beta + c, r.ncol, k, vnorm2, r.eigw + c,
+                                    r.eigw + plane + c, r.eigw + 2 * plane + c, r.ncol);
+}
+
+// Quadratures of every running column, the per-shift mean L_s(i) and the
+// stop rule; one block per shift.  Launched when the quadrature is needed
+// (every step under a tolerance, else only after the last step).
+__global__ void __launch_bounds__(kThreads)
+finish_kernel(Run r, int i, int do_quad, int last)
+{
+    const int s = blockIdx.x;
+    const bool real = s < r.S;
+    if (!real || r.sdone[s]) return;
+    const int cbeg = s * r.m;
+    const int cend = cbeg + r.m;
+    __shared__ double red[kThreads];
+    __shared__ int stop;
+    double lsum = 0.0;
+    for (int c = cbeg + threadIdx.x; c < cend; c += blockDim.x) {
+        if (do_quad) {
             const int k = r.kdone[c] ? min(r.kdone[c], i) : i;
             double q = gauss_quadrature(r, c, k, (double)r.n);
             if (q < 0.0) {
@@ -424,50 +636,61 @@ cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V
 }
 
 template <typename T>
+size_t dots_smem(int i)
+{
+    return (size_t)(DNS + 4) * DSTAGE + (size_t)2 * i * CW * sizeof(double) +
+           (2 * DNS + 4) * sizeof(uint64_t);
+}
+
+template <typename T>
+size_t update_smem(int i)
+{
+    return (size_t)(UNS + 2) * USTAGE + (((size_t)i * CW * sizeof(T) + 15) & ~(size_t)15) +
+           (2 * UNS + 4) * sizeof(uint64_t);
+}
+
+template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st)
 {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(reorth_dots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((2 * kMaxSteps + 2 * WARPS * JB) * CW * sizeof(double)));
+                             (int)dots_smem<T>(kMaxSteps));
         attr_set = true;
     }
-    const size_t smem = ((size_t)2 * i + 2 * WARPS * JB) * CW * sizeof(double);
-    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), kThreads, smem, st>>>(r, i);
+    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), BTHREADS, dots_smem<T>(i), st>>>(r, i);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st)
 {
-    const int tot = r.ncol * i;
-    reorth_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(r, i);
+    reorth_reduce_kernel<<<r.nchunk * i, RW * 32, 0, st>>>(r, i);
     return cudaGetLastError();
 }
 
 cudaError_t launch_coef(const Run& r, int i, cudaStream_t st)
 {
-    reorth_coef_kernel<<<(r.ncol + 127) / 128, 128, 0, st>>>(r, i);
+    const int tot = r.ncol * i;
+    reorth_coef_kernel<<<(tot + 255) / 256, 256, 0, st>>>(r, i);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st)
 {
-    const size_t smem = (size_t)i * CW * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(reorth_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kMaxSteps * CW * sizeof(T)));
+                             (int)update_smem<T>(kMaxSteps));
         attr_set = true;
     }
-    reorth_update_kernel<T><<<dim3(r.nblk, r.nchunk), kThreads, smem, st>>>(r, i);
+    reorth_update_kernel<T><<<dim3(r.nblk, r.nchunk), BTHREADS, update_smem<T>(i), st>>>(r, i);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish(const Run& r, int i, bool do_quad, bool last, cudaStream_t st)
 {
-    const int nb = r.S + (r.ncol > r.ncol_real ? 1 : 0);
-    finish_kernel<<<nb, kThreads, 0, st>>>(r, i, do_quad ? 1 : 0, last ? 1 : 0);
+    finish_kernel<<<r.S, kThreads, 0, st>>>(r, i, do_quad ? 1 : 0, last ? 1 : 0);
     return cudaGetLastError();
 }
 
