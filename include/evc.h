@@ -178,12 +178,20 @@ int evc_sync(evc_ctx* ctx);
 int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
 
 /* Options.
- *   EVC_OPT_GRAPH  : 1 (default) replays the whole multi-step launch sequence
- *                    as one CUDA graph, 0 launches kernels one by one.
- *   EVC_OPT_PROFILE: 1 brackets every kernel launch with a pair of timing
- *                    events on the context's stream (inside the graph when
- *                    graphs are on); 0 (default) records nothing.           */
-enum { EVC_OPT_GRAPH = 1, EVC_OPT_PROFILE = 2 };
+ *   EVC_OPT_GRAPH     : 1 (default) replays the whole multi-step launch
+ *                       sequence as one CUDA graph, 0 launches kernels one by one.
+ *   EVC_OPT_PROFILE   : 1 brackets every kernel launch with a pair of timing
+ *                       events on the context's stream (inside the graph when
+ *                       graphs are on); 0 (default) records nothing.
+ *   EVC_OPT_QUADRATURE: EVC_QUAD_GAUSS (default) uses the Gauss rule of J_k
+ *                       (Sec. 3, Eq. gauss_quad); EVC_QUAD_GA the generalized
+ *                       averaged Gauss rule, i.e. the same weights taken from
+ *                       the (2k-1)-order extension of J_k built by mirroring
+ *                       its coefficients around beta_{k+1} (Sec. 3.4,
+ *                       Eq. GA_Tk).  Same Lanczos steps, different step 5 of
+ *                       Algorithm 2.                                          */
+enum { EVC_OPT_GRAPH = 1, EVC_OPT_PROFILE = 2, EVC_OPT_QUADRATURE = 3 };
+enum { EVC_QUAD_GAUSS = 0, EVC_QUAD_GA = 1 };
 int evc_set_option(evc_ctx* ctx, int option, int64_t value);
 
 /* Kernel classes reported by evc_get_profile.                               */

@@ -361,12 +361,39 @@ double evo_gauss_quad(int k, const double* alpha, const double* beta, double vno
     return vnorm2 * s;
 }
 
+/* Generalized averaged Gauss quadrature (Sec. 3.4, Eq. GA_Tk): the Gauss
+ * formula of Eq. gauss_quad applied to the (2k-1) x (2k-1) tridiagonal with
+ * diagonal (alpha_1..alpha_k, alpha_{k-1}..alpha_1) and off-diagonal
+ * (beta_2..beta_k, beta_{k+1}, beta_{k-1}..beta_2).  beta[k] = beta_{k+1}. */
+double evo_ga_quad(int k, const double* alpha, const double* beta, double vnorm2)
+{
+    if (k <= 1) return evo_gauss_quad(k, alpha, beta, vnorm2);
+    const int kk = 2 * k - 1;
+    double* a2 = (double*)malloc(sizeof(double) * kk);
+    double* b2 = (double*)malloc(sizeof(double) * (kk + 1));
+    double q = 0.0;
+    if (a2 && b2) {
+        /* diagonal: alpha_1 .. alpha_k, then alpha_{k-1} .. alpha_1 */
+        for (int t = 0; t < k; ++t) a2[t] = alpha[t];
+        for (int t = 0; t < k - 1; ++t) a2[k + t] = alpha[k - 2 - t];
+        /* off-diagonal in the beta layout (b2[t] couples t-1 and t) */
+        b2[0] = 0.0;
+        for (int t = 1; t < k; ++t) b2[t] = beta[t];            /* beta_2 .. beta_k  */
+        b2[k] = beta[k];                                         /* beta_{k+1}        */
+        for (int t = 1; t < k - 1; ++t) b2[k + t] = beta[k - 1 - t]; /* beta_{k-1} .. beta_2 */
+        b2[kk] = 0.0;
+        q = evo_gauss_quad(kk, a2, b2, vnorm2);
+    }
+    free(a2); free(b2);
+    return q;
+}
+
 /* ---------------------------------------------------------------- count */
 
-int evo_count(const evo_problem* P, const double* shifts, int S, int m,
-              const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
-              double breakdown_rel, int nthreads,
-              double* quad, int* steps, double* L)
+int evo_count_rule(const evo_problem* P, const double* shifts, int S, int m,
+                   const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
+                   double breakdown_rel, int nthreads, int rule,
+                   double* quad, int* steps, double* L)
 {
     const int64_t n = P->n;
     if (S < 1 || m < 1 || kmax < 1 || n < 1) return -1;
@@ -396,7 +423,8 @@ int evo_count(const evo_problem* P, const double* shifts, int S, int m,
             for (int i = 1; i <= kmax; ++i) {
                 if (tol <= 0.0 && i < kmax) continue;   /* only the last step is needed */
                 int ki = i < kd ? i : kd;               /* after breakdown J stays J_kd */
-                quad_hist[(size_t)c * kmax + (i - 1)] = evo_gauss_quad(ki, alpha, beta, vn2);
+                quad_hist[(size_t)c * kmax + (i - 1)] =
+                    rule == 1 ? evo_ga_quad(ki, alpha, beta, vn2) : evo_gauss_quad(ki, alpha, beta, vn2);
             }
         }
         free(v); free(alpha); free(beta);
@@ -424,4 +452,13 @@ int evo_count(const evo_problem* P, const double* shifts, int S, int m,
     }
     free(quad_hist);
     return 0;
+}
+
+int evo_count(const evo_problem* P, const double* shifts, int S, int m,
+              const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
+              double breakdown_rel, int nthreads,
+              double* quad, int* steps, double* L)
+{
+    return evo_count_rule(P, shifts, S, m, probe_ids, kmax, tol, seed, breakdown_rel, nthreads, 0,
+                          quad, steps, L);
 }

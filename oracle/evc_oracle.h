@@ -90,6 +90,11 @@ int evo_tridiag_eig(int k, const double* alpha, const double* beta,
 /* Gauss quadrature ||v||^2 sum_{theta_i < 0} z_i(1)^2 from J_k. */
 double evo_gauss_quad(int k, const double* alpha, const double* beta, double vnorm2);
 
+/* Generalized averaged Gauss quadrature (Sec. 3.4, Eq. GA_Tk) from J_{k+1,k}:
+ * the Gauss formula on the mirrored (2k-1) x (2k-1) extension; beta[k] =
+ * beta_{k+1} is used. */
+double evo_ga_quad(int k, const double* alpha, const double* beta, double vnorm2);
+
 /* The estimator L_tau(k, m) for S shifts with m probes each.
  * Column (s, j) uses probe id probe_ids[j] (or j if probe_ids is NULL) and the
  * seeded Rademacher probe above; the same probes serve every shift.
@@ -101,6 +106,12 @@ int evo_count(const evo_problem* P, const double* shifts, int S, int m,
               const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
               double breakdown_rel, int nthreads,
               double* quad, int* steps, double* L);
+/* Same with the quadrature rule chosen: rule 0 = Gauss, 1 = generalized
+ * averaged Gauss. */
+int evo_count_rule(const evo_problem* P, const double* shifts, int S, int m,
+                   const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
+                   double breakdown_rel, int nthreads, int rule,
+                   double* quad, int* steps, double* L);
 
 #ifdef __cplusplus
 }

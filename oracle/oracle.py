@@ -82,6 +82,11 @@ def _load():
             lib.evo_count.argtypes = [P, d, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                       C.c_uint64, C.c_double, C.c_int, d,
                                       C.POINTER(C.c_int), d]
+            lib.evo_count_rule.argtypes = [P, d, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                           C.c_double, C.c_uint64, C.c_double, C.c_int, C.c_int,
+                                           d, C.POINTER(C.c_int), d]
+            lib.evo_ga_quad.restype = C.c_double
+            lib.evo_ga_quad.argtypes = [C.c_int, d, d, C.c_double]
             _lib = lib
     return _lib
 
@@ -216,9 +221,20 @@ def gauss_quad(alpha, beta, vnorm2):
     return float(_load().evo_gauss_quad(k, _dp(alpha), _dp(beta), vnorm2))
 
 
+def ga_quad(alpha, beta, vnorm2):
+    """Generalized averaged Gauss quadrature from alpha[k], beta[k+1]."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    assert beta.size >= alpha.size + 1
+    return float(_load().evo_ga_quad(alpha.size, _dp(alpha), _dp(beta), vnorm2))
+
+
 def count(P: Problem, shifts, m, kmax, tol=0.0, seed=0, probe_ids=None,
-          breakdown_rel=BREAKDOWN_REL, nthreads=0):
-    """Algorithm 2 for every shift: returns (quad[S, m], steps[S], L[S])."""
+          breakdown_rel=BREAKDOWN_REL, nthreads=0, rule=0):
+    """Algorithm 2 for every shift: returns (quad[S, m], steps[S], L[S]).
+
+    rule 0: Gauss quadrature (Eq. gauss_quad); 1: generalized averaged Gauss
+    (Sec. 3.4)."""
     shifts = np.ascontiguousarray(shifts, dtype=np.float64)
     S = shifts.size
     quad = np.zeros(S * m)
@@ -228,9 +244,9 @@ def count(P: Problem, shifts, m, kmax, tol=0.0, seed=0, probe_ids=None,
     if probe_ids is not None:
         pid = np.ascontiguousarray(probe_ids, dtype=np.int64)
         assert pid.size == m
-    rc = _load().evo_count(P.ref, _dp(shifts), S, m,
-                           pid.ctypes.data if pid is not None else None, kmax, tol,
-                           C.c_uint64(seed), breakdown_rel, nthreads, _dp(quad),
-                           steps.ctypes.data_as(C.POINTER(C.c_int)), _dp(L))
+    rc = _load().evo_count_rule(P.ref, _dp(shifts), S, m,
+                                pid.ctypes.data if pid is not None else None, kmax, tol,
+                                C.c_uint64(seed), breakdown_rel, nthreads, int(rule), _dp(quad),
+                                steps.ctypes.data_as(C.POINTER(C.c_int)), _dp(L))
     assert rc == 0, rc
     return quad.reshape(S, m), steps, L

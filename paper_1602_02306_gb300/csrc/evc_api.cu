@@ -67,6 +67,7 @@ struct evc_ctx {
     double cheb_a = 0, cheb_b = 0;
     std::vector<double> cheb_coef;
     int prec_version = 0;
+    int quad_rule = EVC_QUAD_GAUSS;
     // workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -189,11 +190,11 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.hbuf = D((size_t)kmax * ncol);
     r.gram = D((size_t)kmax * (kmax + 1) / 2 * ncol);
     r.part_nrm = D((size_t)nchunk * nblk * CW);
-    r.eigw = D((size_t)3 * kmax * ncol);
     r.err = I(1);
     r.seed = reinterpret_cast<uint64_t*>(take(8));
     r.tol = D(1);
     r.breakdown_rel = c->precision == EVC_FP64 ? 1e-12 : 1e-6;
+    r.ga = c->quad_rule == EVC_QUAD_GA ? 1 : 0;
     return off;
 }
 
@@ -521,7 +522,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         const bool last = (i == r.kmax);
         if (!rc && (adaptive || last))
             rc = rec(ctx, EVC_K_FINISH, i, colb * (2.0 * i + 2),
-                     [&] { return launch_finish(r, i, true, last, st); });
+                     [&] { return launch_finish(r, i, last, st); });
         if (!rc && adaptive) rc = rec(ctx, EVC_K_FINISH, i, colb, [&] { return launch_active(r, st); });
     }
     return rc;
@@ -1052,6 +1053,14 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
     }
     if (option == EVC_OPT_PROFILE) {
         ctx->profile = value != 0;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_QUADRATURE) {
+        if (value != EVC_QUAD_GAUSS && value != EVC_QUAD_GA)
+            return fail(ctx, EVC_EINVAL, "unknown quadrature rule %lld", (long long)value);
+        ctx->quad_rule = (int)value;
+        ++ctx->prec_version;   // part of the captured graph
         drop_graph(ctx);
         return EVC_OK;
     }

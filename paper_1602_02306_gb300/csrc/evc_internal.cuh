@@ -62,12 +62,12 @@ struct Run {
     double* hbuf;            // [kmax][ncol]  h_j = q_j . w of the current step
     double* gram;            // [kmax(kmax+1)/2][ncol]  G_ab = q_a . q_b, a >= b
     double* part_nrm;        // [nchunk][nblk][CW]
-    double* eigw;            // [3][kmax][ncol]  eigensolver scratch
     void* jac;               // T[S][n]  (Jacobi scales, when used)
     // device scalars, rewritten before each replay
     uint64_t* seed;          // [1]
     double* tol;             // [1]
     double breakdown_rel;
+    int ga;                  // 1: generalized averaged Gauss quadrature (Sec. 3.4)
 };
 
 // Coefficients of one stencil pass (see evc_stencil.cu):
@@ -120,7 +120,7 @@ template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_coef(const Run& r, int i, cudaStream_t st);
-cudaError_t launch_finish(const Run& r, int i, bool do_quad, bool last, cudaStream_t st);
+cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st);
 cudaError_t launch_active(const Run& r, cudaStream_t st);
 
 // Host-side helpers.

@@ -526,43 +526,46 @@ reorth_update_kernel(Run r, int i)
     if (threadIdx.x == 0) r.cnt_upd[ch] = 0;
 }
 
-// Gauss quadrature of column c's J_k; eigensolver scratch in the workspace,
-// [3][kmax][ncol] (coalesced across columns).
-__device__ double gauss_quadrature(const Run& r, int c, int k, double vnorm2)
+// Quadrature of every running column's J_i (Sec. 3, Eq. gauss_quad), or of
+// the extended J~_{2i-1} of the generalized averaged rule (Sec. 3.4,
+// Eq. GA_Tk) when r.ga is set.  One thread per column; the eigensolver
+// scratch (3 x rule size per column) lives in shared memory.
+__global__ void quad_kernel(Run r, int i)
 {
-    const int64_t plane = (int64_t)r.kmax * r.ncol;
-    return tridiag_gauss_quadrature(r.alpha + c, r.beta + c, r.ncol, k, vnorm2, r.eigw + c,
-                                    r.eigw + plane + c, r.eigw + 2 * plane + c, r.ncol);
+    extern __shared__ double qs[];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= r.ncol_real) return;
+    if (r.sdone[r.shift_of[c]]) return;
+    const int k = r.kdone[c] ? min(r.kdone[c], i) : i;
+    const int nb = blockDim.x;
+    const int kk = r.ga ? 2 * r.kmax - 1 : r.kmax;
+    double* d = qs + threadIdx.x;
+    double* e = qs + (size_t)kk * nb + threadIdx.x;
+    double* z = qs + (size_t)2 * kk * nb + threadIdx.x;
+    double q = r.ga ? tridiag_ga_quadrature(r.alpha + c, r.beta + c, r.ncol, k, (double)r.n, d, e, z, nb)
+                    : tridiag_gauss_quadrature(r.alpha + c, r.beta + c, r.ncol, k, (double)r.n, d, e,
+                                               z, nb);
+    if (q < 0.0) {
+        atomicExch(r.err, DERR_NUMERIC);
+        q = 0.0;
+    }
+    r.quad[c] = q;
 }
 
-// Quadratures of every running column, the per-shift mean L_s(i) and the
-// stop rule; one block per shift.  Launched when the quadrature is needed
-// (every step under a tolerance, else only after the last step).
+// Per-shift mean L_s(i) = (1/m) sum_j quad_j in a fixed tree, and the stop
+// rule: a shift stops at the last step or, under a tolerance, at the first
+// i >= 2 with |L_s(i) - L_s(i-1)| <= tol.  A stopped shift's columns are
+// frozen (their later vectors become exact zeros).  One block per shift.
 __global__ void __launch_bounds__(kThreads)
-finish_kernel(Run r, int i, int do_quad, int last)
+shift_kernel(Run r, int i, int last)
 {
     const int s = blockIdx.x;
-    const bool real = s < r.S;
-    if (!real || r.sdone[s]) return;
-    const int cbeg = s * r.m;
-    const int cend = cbeg + r.m;
+    if (r.sdone[s]) return;
+    const int cbeg = s * r.m, cend = cbeg + r.m;
     __shared__ double red[kThreads];
     __shared__ int stop;
     double lsum = 0.0;
-    for (int c = cbeg + threadIdx.x; c < cend; c += blockDim.x) {
-        if (do_quad) {
-            const int k = r.kdone[c] ? min(r.kdone[c], i) : i;
-            double q = gauss_quadrature(r, c, k, (double)r.n);
-            if (q < 0.0) {
-                atomicExch(r.err, DERR_NUMERIC);
-                q = 0.0;
-            }
-            r.quad[c] = q;
-            lsum += q;
-        }
-    }
-    if (!real || !do_quad) return;
-    // L_s(i) = mean_j quad_j: fixed-shape shared-memory tree
+    for (int c = cbeg + threadIdx.x; c < cend; c += blockDim.x) lsum += r.quad[c];
     red[threadIdx.x] = lsum;
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
@@ -585,7 +588,6 @@ finish_kernel(Run r, int i, int do_quad, int last)
     __syncthreads();
     if (stop)
         for (int c = cbeg + threadIdx.x; c < cend; c += blockDim.x) {
-            // freeze the column: its later vectors become exact zeros
             r.quad_final[c] = r.quad[c];
             r.ppc[c] = 0.0;
             for (int j = i; j <= r.kmax; ++j) r.scl[(int64_t)j * r.ncol + c] = 0.0;
@@ -688,9 +690,23 @@ cudaError_t launch_update(const Run& r, int i, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const Run& r, int i, bool do_quad, bool last, cudaStream_t st)
+cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st)
 {
-    finish_kernel<<<r.S, kThreads, 0, st>>>(r, i, do_quad ? 1 : 0, last ? 1 : 0);
+    // The eigensolves are chains of dependent FP64 operations: spread the
+    // columns over all 152 SMs (few threads per block) so each one has an
+    // SM's FP64 pipes to itself; 3 scratch vectors per thread must fit in 96 KB.
+    const int kk = r.ga ? 2 * r.kmax - 1 : r.kmax;
+    int qb = 1;
+    while (qb < 32 && qb * 2 * 152 <= r.ncol_real) qb <<= 1;
+    while (qb > 1 && (size_t)qb * 3 * kk * sizeof(double) > 96 * 1024) qb >>= 1;
+    const size_t smem = (size_t)qb * 3 * kk * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        attr_set = true;
+    }
+    quad_kernel<<<(r.ncol_real + qb - 1) / qb, qb, smem, st>>>(r, i);
+    shift_kernel<<<r.S, kThreads, 0, st>>>(r, i, last ? 1 : 0);
     return cudaGetLastError();
 }
 

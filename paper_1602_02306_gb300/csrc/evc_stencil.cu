@@ -10,9 +10,12 @@
 //
 // Layout: X[chunk][p][32] with p = x + N*(y + N*z).  Each thread owns one
 // 16-byte vector of columns (4 FP32 or 2 FP64 probes) of one (x, y) line and
-// marches along z keeping the z-neighbours in a register window; x/y
-// neighbours come through L1.  The pass is HBM-bound: it streams the operand
-// once and the pointwise operands once.
+// marches along z keeping the z-neighbours in a register window.  The loads
+// of plane z + D (in-plane neighbours, the next window plane, the pointwise
+// operands) are issued as asynchronous 16-byte copies (cp.async) into the
+// thread's own shared-memory slots while plane z is computed, so the bytes
+// in flight are held by shared memory rather than registers.  The pass is
+// HBM-bound: it streams the operand once and the pointwise operands once.
 #include "evc_internal.cuh"
 
 #include <cstring>
@@ -51,8 +54,21 @@ __device__ __forceinline__ void st_pack(Pack<T>* p, const Pack<T>& v)
     *reinterpret_cast<typename Vec16<T>::type*>(p) = t;
 }
 
-constexpr int TX = 8;     // points per block along x
-constexpr int ZB = 16;    // z planes per block
+constexpr int ZB = 32;     // z planes per block
+constexpr int STH = 128;   // threads per block
+constexpr int DEPTH = 3;   // planes of loads in flight ahead of the one computed
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    // 16-byte asynchronous copy global -> shared, cached in L1 (neighbour reuse)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
 
 struct KArgs {
     StencilPass p;
@@ -64,25 +80,37 @@ struct KArgs {
     int64_t n;
 };
 
-template <typename T, int R, bool JAC>
-__global__ void __launch_bounds__(kThreads, R == 1 ? 4 : 3)
+// Operand set of a pass, a compile-time mask so that absent operands cost
+// neither instructions nor registers.
+enum { HAS_X = 1, HAS_PREV = 2, HAS_PP = 4, HAS_VS = 8 };
+
+template <typename T, int R, bool JAC, int MASK>
+__global__ void __launch_bounds__(STH)
 stencil_pass_kernel(KArgs a)
 {
     constexpr int W = 16 / sizeof(T);        // columns per thread
     constexpr int LPP = CW / W;              // threads per grid point
-    constexpr int TY = kThreads / LPP / TX;  // points per block along y
+    constexpr int TX = 8;                    // points per block along x
+    constexpr int TY = STH / LPP / TX;       // points per block along y
+    constexpr bool X = MASK & HAS_X, PREV = MASK & HAS_PREV, PP = MASK & HAS_PP,
+                   VS = MASK & HAS_VS;
+    // loads per plane: 4R in-plane neighbours, the next window plane, pointwise operands
+    constexpr int NL = 4 * R + 1 + (X ? 1 : 0) + (PREV ? 1 : 0) + (PP ? 1 : 0);
+    constexpr int UC = 4 * R, UX = UC + 1, UP = UX + (X ? 1 : 0), UPP = UP + (PREV ? 1 : 0);
     const int ch = blockIdx.z;
     if (!a.chunk_active[ch]) return;
+    extern __shared__ __align__(16) unsigned char st_raw[];
+    Pack<T>* slots = reinterpret_cast<Pack<T>*>(st_raw);      // [DEPTH+1][NL][STH]
     // per-column constants of this chunk, shared by the block
     __shared__ Pack<T> s_sig[LPP], s_insc[LPP], s_a0s[LPP], s_ppc[LPP];
     __shared__ int s_shift[CW];
     if (threadIdx.x < CW) {
         const int c = ch * CW + threadIdx.x;
         const int l = threadIdx.x / W, w = threadIdx.x % W;
-        s_sig[l].v[w] = a.p.useSigma ? (T)a.sigma[c] : (T)0;
+        s_sig[l].v[w] = VS ? (T)a.sigma[c] : (T)0;
         s_insc[l].v[w] = a.p.insc ? (T)a.p.insc[c] : (T)1;
         s_a0s[l].v[w] = (T)(a.p.a0 * (a.p.xs ? a.p.xs[c] : 1.0));
-        s_ppc[l].v[w] = a.p.ppc ? (T)a.p.ppc[c] : (T)0;
+        s_ppc[l].v[w] = PP ? (T)a.p.ppc[c] : (T)0;
         s_shift[threadIdx.x] = JAC ? a.shift_of[c] : 0;
     }
     __syncthreads();
@@ -96,76 +124,98 @@ stencil_pass_kernel(KArgs a)
     const int z0 = blockIdx.y * ZB;
     const int z1 = min(z0 + ZB, N);
     const int64_t n = a.n;
+    const int64_t NN = (int64_t)N * N;
 
-    const Pack<T>* __restrict__ in = reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* in = reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.in) + ch * a.p.in_cs) + lane;
-    const Pack<T>* __restrict__ xv = a.p.x ? reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* xv = X ? reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.x) + ch * a.p.x_cs) + lane : nullptr;
-    const Pack<T>* pv = a.p.prev ? reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* pv = PREV ? reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.prev) + ch * a.p.prev_cs) + lane : nullptr;
-    const Pack<T>* __restrict__ ppv = a.p.pp ? reinterpret_cast<const Pack<T>*>(
+    const Pack<T>* ppv = PP ? reinterpret_cast<const Pack<T>*>(
         static_cast<const T*>(a.p.pp) + ch * a.p.pp_cs) + lane : nullptr;
     Pack<T>* out = reinterpret_cast<Pack<T>*>(static_cast<T*>(a.p.out) + ch * a.p.out_cs) + lane;
     const T* __restrict__ V = static_cast<const T*>(a.op.V);
     const T* __restrict__ jac = static_cast<const T*>(a.jac);
+    const int sbase = lane * W;
+
+    // wrapped in-plane neighbour offsets (points), fixed along the z march
+    const int xm1 = x == 0 ? N - 1 : x - 1, xp1 = x == N - 1 ? 0 : x + 1;
+    const int ym1 = y == 0 ? N - 1 : y - 1, yp1 = y == N - 1 ? 0 : y + 1;
+    const int64_t cxy = x + (int64_t)N * y;
+    int64_t nbo[4 * R];
+    nbo[0] = xm1 + (int64_t)N * y;
+    nbo[1] = xp1 + (int64_t)N * y;
+    nbo[2] = x + (int64_t)N * ym1;
+    nbo[3] = x + (int64_t)N * yp1;
+    if (R == 2) {
+        nbo[4 % (4 * R)] = (x + N - 2) % N + (int64_t)N * y;
+        nbo[5 % (4 * R)] = (x + 2) % N + (int64_t)N * y;
+        nbo[6 % (4 * R)] = x + (int64_t)N * ((y + N - 2) % N);
+        nbo[7 % (4 * R)] = x + (int64_t)N * ((y + 2) % N);
+    }
+    auto slot = [&](int stage, int u) -> Pack<T>* {
+        return slots + ((size_t)stage * NL + u) * STH + threadIdx.x;
+    };
+    auto jscale = [&](Pack<T>& v, int64_t q) {
+        if (JAC) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) v.v[w] *= __ldg(jac + (int64_t)s_shift[sbase + w] * n + q);
+        }
+    };
+    // issue the loads of plane zz into stage st (one commit group per plane;
+    // an empty group past the end keeps the group count uniform)
+    // source pointers of the next plane to issue, advanced one plane per issue
+    const int64_t pstep = NN * LPP;
+    const Pack<T>* src_nb[4 * R];
+#pragma unroll
+    for (int u = 0; u < 4 * R; ++u) src_nb[u] = in + (nbo[u] + NN * z0) * LPP;
+    const Pack<T>* src_x = X ? xv + (cxy + NN * z0) * LPP : nullptr;
+    const Pack<T>* src_p = PREV ? pv + (cxy + NN * z0) * LPP : nullptr;
+    const Pack<T>* src_pp = PP ? ppv + (cxy + NN * z0) * LPP : nullptr;
+    auto issue = [&](int zz, int st) {
+        if (zz < z1) {
+#pragma unroll
+            for (int u = 0; u < 4 * R; ++u) {
+                cp_async16(slot(st, u), src_nb[u]);
+                src_nb[u] += pstep;
+            }
+            if (zz + 1 < z1) cp_async16(slot(st, UC), in + (cxy + NN * ((zz + 1 + R) % N)) * LPP);
+            if (X) { cp_async16(slot(st, UX), src_x); src_x += pstep; }
+            if (PREV) { cp_async16(slot(st, UP), src_p); src_p += pstep; }
+            if (PP) { cp_async16(slot(st, UPP), src_pp); src_pp += pstep; }
+        }
+        cp_async_commit();
+    };
+
+    Pack<T> win[2 * R + 1];
+#pragma unroll
+    for (int o = -R; o <= R; ++o) {
+        const int64_t q = cxy + NN * (((z0 + o) % N + N) % N);
+        win[o + R] = ldg_pack(in + q * LPP);
+        jscale(win[o + R], q);
+    }
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) issue(z0 + d, d);
 
     const T k1 = (T)a.p.k1;
     const T c1 = (T)a.op.c1, c2 = (T)a.op.c2;
     const T dg = (T)(a.p.k1 * a.op.cd + a.p.k0);
     const T a2 = (T)a.p.a2;
 
-    // wrapped in-plane neighbour coordinates
-    const int xm1 = x == 0 ? N - 1 : x - 1, xp1 = x == N - 1 ? 0 : x + 1;
-    const int ym1 = y == 0 ? N - 1 : y - 1, yp1 = y == N - 1 ? 0 : y + 1;
-    const int xm2 = (x + N - 2) % N, xp2 = (x + 2) % N;
-    const int ym2 = (y + N - 2) % N, yp2 = (y + 2) % N;
-    const int64_t NN = (int64_t)N * N;
-    const int64_t cxy = x + (int64_t)N * y;
-    const int64_t oxm1 = xm1 + (int64_t)N * y, oxp1 = xp1 + (int64_t)N * y;
-    const int64_t oym1 = x + (int64_t)N * ym1, oyp1 = x + (int64_t)N * yp1;
-    const int64_t oxm2 = xm2 + (int64_t)N * y, oxp2 = xp2 + (int64_t)N * y;
-    const int64_t oym2 = x + (int64_t)N * ym2, oyp2 = x + (int64_t)N * yp2;
-    const int sbase = lane * W;
-
-    auto load = [&](int64_t q) -> Pack<T> {
-        Pack<T> v = ldg_pack(in + q * LPP);
-        if (JAC) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) v.v[w] *= __ldg(jac + (int64_t)s_shift[sbase + w] * n + q);
-        }
-        return v;
-    };
-
-    Pack<T> win[2 * R + 1];
-#pragma unroll
-    for (int o = -R; o <= R; ++o) {
-        const int zz = ((z0 + o) % N + N) % N;
-        win[o + R] = load(cxy + NN * zz);
-    }
-
     for (int z = z0; z < z1; ++z) {
+        const int stg = (z - z0) % (DEPTH + 1);
+        issue(z + DEPTH, (z - z0 + DEPTH) % (DEPTH + 1));
+        cp_async_wait<DEPTH>();                  // plane z has landed (own copies)
         const int64_t rowz = NN * z;
         const int64_t p = cxy + rowz;
-        // every load of this plane first: they are independent
         Pack<T> nb[4 * R];
-        nb[0] = load(oxm1 + rowz);
-        nb[1] = load(oxp1 + rowz);
-        nb[2] = load(oym1 + rowz);
-        nb[3] = load(oyp1 + rowz);
-        if (R == 2) {
-            nb[4 % (4 * R)] = load(oxm2 + rowz);
-            nb[5 % (4 * R)] = load(oxp2 + rowz);
-            nb[6 % (4 * R)] = load(oym2 + rowz);
-            nb[7 % (4 * R)] = load(oyp2 + rowz);
+#pragma unroll
+        for (int u = 0; u < 4 * R; ++u) {
+            nb[u] = *slot(stg, u);
+            jscale(nb[u], nbo[u] + rowz);
         }
-        const bool more = z + 1 < z1;
-        Pack<T> nxt;
-        if (more) nxt = load(cxy + NN * ((z + 1 + R) % N));
-        Pack<T> tx, tp, tpp;
-        if (xv) tx = ldg_pack(xv + p * LPP);
-        if (pv) tp = ld_pack(pv + p * LPP);
-        if (ppv) tpp = ldg_pack(ppv + p * LPP);
-        const T vp = a.p.useV ? __ldg(V + p) : (T)0;
+        const T vp = VS ? __ldg(V + p) : (T)0;
         T mp[W];
         if (JAC) {
 #pragma unroll
@@ -184,27 +234,69 @@ stencil_pass_kernel(KArgs a)
             if (JAC) st *= mp[w];
             res.v[w] = insc.v[w] * st;
         }
-        if (xv) {
-            const Pack<T> a0s = s_a0s[lane];
+        if (X) {
+            const Pack<T> t = *slot(stg, UX), c = s_a0s[lane];
 #pragma unroll
-            for (int w = 0; w < W; ++w) res.v[w] += a0s.v[w] * tx.v[w];
+            for (int w = 0; w < W; ++w) res.v[w] += c.v[w] * t.v[w];
         }
-        if (pv) {
+        if (PREV) {
+            const Pack<T> t = *slot(stg, UP);
 #pragma unroll
-            for (int w = 0; w < W; ++w) res.v[w] -= a2 * tp.v[w];
+            for (int w = 0; w < W; ++w) res.v[w] -= a2 * t.v[w];
         }
-        if (ppv) {
-            const Pack<T> ppc = s_ppc[lane];
+        if (PP) {
+            const Pack<T> t = *slot(stg, UPP), c = s_ppc[lane];
 #pragma unroll
-            for (int w = 0; w < W; ++w) res.v[w] -= ppc.v[w] * tpp.v[w];
+            for (int w = 0; w < W; ++w) res.v[w] -= c.v[w] * t.v[w];
         }
         st_pack(out + p * LPP, res);
-        if (more) {
+        if (z + 1 < z1) {
+            Pack<T> nxt = *slot(stg, UC);
+            jscale(nxt, cxy + NN * ((z + 1 + R) % N));
 #pragma unroll
             for (int o = 0; o < 2 * R; ++o) win[o] = win[o + 1];
             win[2 * R] = nxt;
         }
     }
+    cp_async_wait<0>();
+}
+
+template <int R, int MASK>
+constexpr int stencil_loads()
+{
+    return 4 * R + 1 + ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) +
+           ((MASK & HAS_PP) ? 1 : 0);
+}
+
+template <typename T, int R, bool JAC, int MASK>
+void launch_one(dim3 grid, cudaStream_t st, const KArgs& a)
+{
+    constexpr size_t smem = (size_t)(DEPTH + 1) * stencil_loads<R, MASK>() * STH * 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(stencil_pass_kernel<T, R, JAC, MASK>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    stencil_pass_kernel<T, R, JAC, MASK><<<grid, STH, smem, st>>>(a);
+}
+
+template <typename T, int R, bool JAC>
+bool launch_masked(int mask, dim3 grid, cudaStream_t st, const KArgs& a)
+{
+    switch (mask) {
+    case 0: launch_one<T, R, JAC, 0>(grid, st, a); break;
+    case HAS_X: launch_one<T, R, JAC, HAS_X>(grid, st, a); break;
+    case HAS_X | HAS_PREV: launch_one<T, R, JAC, HAS_X | HAS_PREV>(grid, st, a); break;
+    case HAS_X | HAS_PP: launch_one<T, R, JAC, HAS_X | HAS_PP>(grid, st, a); break;
+    case HAS_X | HAS_PREV | HAS_PP: launch_one<T, R, JAC, HAS_X | HAS_PREV | HAS_PP>(grid, st, a); break;
+    case HAS_PP: launch_one<T, R, JAC, HAS_PP>(grid, st, a); break;
+    case HAS_VS: launch_one<T, R, JAC, HAS_VS>(grid, st, a); break;
+    case HAS_VS | HAS_PP: launch_one<T, R, JAC, HAS_VS | HAS_PP>(grid, st, a); break;
+    default:
+        return false;   // not an operand set the library issues
+    }
+    return true;
 }
 
 }  // namespace
@@ -215,7 +307,8 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
 {
     constexpr int W = 16 / sizeof(T);
     constexpr int LPP = CW / W;
-    constexpr int TY = kThreads / LPP / TX;
+    constexpr int TX = 8;
+    constexpr int TY = STH / LPP / TX;
     KArgs a;
     a.p = p;
     a.op = op;
@@ -226,13 +319,18 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     a.n = r.n;
     const int N = op.N;
     dim3 grid(((N + TX - 1) / TX) * ((N + TY - 1) / TY), (N + ZB - 1) / ZB, r.nchunk);
-    if (op.order == 2) {
-        if (jacobi) stencil_pass_kernel<T, 1, true><<<grid, kThreads, 0, st>>>(a);
-        else stencil_pass_kernel<T, 1, false><<<grid, kThreads, 0, st>>>(a);
-    } else {
-        if (jacobi) stencil_pass_kernel<T, 2, true><<<grid, kThreads, 0, st>>>(a);
-        else stencil_pass_kernel<T, 2, false><<<grid, kThreads, 0, st>>>(a);
-    }
+    // V and the per-column shift always enter together (the H - sigma I pass)
+    if (p.useV != p.useSigma) return cudaErrorInvalidValue;
+    const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |
+                     (p.useV ? HAS_VS : 0);
+    bool ok;
+    if (op.order == 2)
+        ok = jacobi ? launch_masked<T, 1, true>(mask, grid, st, a)
+                    : launch_masked<T, 1, false>(mask, grid, st, a);
+    else
+        ok = jacobi ? launch_masked<T, 2, true>(mask, grid, st, a)
+                    : launch_masked<T, 2, false>(mask, grid, st, a);
+    if (!ok) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

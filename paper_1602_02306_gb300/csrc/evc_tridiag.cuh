@@ -14,23 +14,19 @@ struct Strided {
     __device__ double& operator[](int t) const { return p[(int64_t)t * s]; }
 };
 
-// alpha[t*astride] = alpha_{t+1} (t < k), beta[t*astride] = beta_{t+1}
-// (beta[0] unused); d, e, z: scratch of k entries each with stride sstride.
-// Eigenvalues by the implicit symmetric QR iteration with Wilkinson shifts
-// on the unreduced trailing block; the first components of the eigenvectors
-// are carried along by applying every Givens rotation to the vector e_1
-// (Golub & Welsch).  Returns -1 if it does not converge.
-__device__ inline double tridiag_gauss_quadrature(const double* alpha, const double* beta,
-                                                  int64_t astride, int k, double vnorm2,
-                                                  double* dp, double* ep, double* zp,
-                                                  int64_t sstride)
+// Quadrature from a tridiagonal already in scratch: d[0..k) diagonal,
+// e[0..k-1) off-diagonal (e[t] couples t and t+1), z scratch of k entries,
+// all with stride sstride.  Eigenvalues by the implicit symmetric QR
+// iteration with Wilkinson shifts on the unreduced trailing block; the first
+// components of the eigenvectors are carried along by applying every Givens
+// rotation to the vector e_1 (Golub & Welsch).  Returns
+// vnorm2 * sum_{theta<0} z(1)^2, or -1 if the iteration does not converge.
+__device__ inline double tridiag_quadrature_inplace(double* dp, double* ep, double* zp,
+                                                   int64_t sstride, int k, double vnorm2)
 {
     const Strided d{dp, sstride}, e{ep, sstride}, z{zp, sstride};
-    for (int t = 0; t < k; ++t) {
-        d[t] = alpha[(int64_t)t * astride];
-        e[t] = t + 1 < k ? beta[(int64_t)(t + 1) * astride] : 0.0;
-        z[t] = t == 0 ? 1.0 : 0.0;
-    }
+    for (int t = 0; t < k; ++t) z[t] = t == 0 ? 1.0 : 0.0;
+    if (k > 0) e[k - 1] = 0.0;
     const double eps = 2.220446049250313e-16;
     int hi = k - 1;
     int iter = 0;
@@ -47,15 +43,17 @@ __device__ inline double tridiag_gauss_quadrature(const double* alpha, const dou
         // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
         const double dl = 0.5 * (d[hi - 1] - d[hi]);
         const double eh = e[hi - 1];
-        const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * hypot(dl, eh);
+        const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * sqrt(dl * dl + eh * eh);
         const double mu = d[hi] - eh * eh / den;
         // implicit QR step on [lo, hi]: chase the bulge down the band
         double xv = d[lo] - mu, yv = e[lo];
         double bulge = 0.0;
         for (int t = lo; t < hi; ++t) {
-            const double rr = hypot(xv, yv);
-            const double cs = rr == 0.0 ? 1.0 : xv / rr;
-            const double sn = rr == 0.0 ? 0.0 : yv / rr;
+            // Lanczos coefficients are O(||C||): no scaling against overflow needed
+            const double rr = sqrt(xv * xv + yv * yv);
+            const double inv = rr == 0.0 ? 0.0 : 1.0 / rr;
+            const double cs = rr == 0.0 ? 1.0 : xv * inv;
+            const double sn = yv * inv;
             if (t > lo) e[t - 1] = rr;                    // (t, t-1) after the rotation
             const double a = d[t], b = e[t], dd = d[t + 1];
             d[t] = cs * cs * a + 2.0 * cs * sn * b + sn * sn * dd;
@@ -76,6 +74,44 @@ __device__ inline double tridiag_gauss_quadrature(const double* alpha, const dou
     for (int t = 0; t < k; ++t)
         if (d[t] < 0.0) s += z[t] * z[t];                // h(theta) = 1 iff theta < 0
     return vnorm2 * s;
+}
+
+// Gauss quadrature of J_k (Sec. 3, Eq. gauss_quad): alpha[t*astride] =
+// alpha_{t+1} (t < k), beta[t*astride] = beta_{t+1} (beta[0] unused); d, e,
+// z: scratch of k entries each with stride sstride.
+__device__ inline double tridiag_gauss_quadrature(const double* alpha, const double* beta,
+                                                  int64_t astride, int k, double vnorm2,
+                                                  double* dp, double* ep, double* zp,
+                                                  int64_t sstride)
+{
+    for (int t = 0; t < k; ++t) {
+        dp[(int64_t)t * sstride] = alpha[(int64_t)t * astride];
+        ep[(int64_t)t * sstride] = t + 1 < k ? beta[(int64_t)(t + 1) * astride] : 0.0;
+    }
+    return tridiag_quadrature_inplace(dp, ep, zp, sstride, k, vnorm2);
+}
+
+// Generalized averaged Gauss quadrature (Sec. 3.4, Eq. GA_Tk): the same rule
+// on the (2k-1) x (2k-1) tridiagonal with diagonal (alpha_1..alpha_k,
+// alpha_{k-1}..alpha_1) and off-diagonal (beta_2..beta_k, beta_{k+1},
+// beta_{k-1}..beta_2).  Needs beta_{k+1} = beta[k*astride]; scratch of 2k-1
+// entries.  For k = 1 it is the Gauss rule.
+__device__ inline double tridiag_ga_quadrature(const double* alpha, const double* beta,
+                                               int64_t astride, int k, double vnorm2,
+                                               double* dp, double* ep, double* zp,
+                                               int64_t sstride)
+{
+    const int kk = 2 * k - 1;
+    for (int t = 0; t < kk; ++t) {
+        const int a = t < k ? t : 2 * k - 2 - t;               // mirrored alpha index
+        dp[(int64_t)t * sstride] = alpha[(int64_t)a * astride];
+        double off = 0.0;
+        if (t < k - 1) off = beta[(int64_t)(t + 1) * astride];            // beta_{t+2}
+        else if (t == k - 1) off = kk > 1 ? beta[(int64_t)k * astride] : 0.0;   // beta_{k+1}
+        else if (t < kk - 1) off = beta[(int64_t)(2 * k - 2 - t) * astride];   // mirrored
+        ep[(int64_t)t * sstride] = off;
+    }
+    return tridiag_quadrature_inplace(dp, ep, zp, sstride, kk, vnorm2);
 }
 
 }  // namespace evc

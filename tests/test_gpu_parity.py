@@ -275,3 +275,42 @@ def test_invalid_arguments_return_status():
     ci2[3] = 99
     with pytest.raises(evc.EvcError):
         evc.evc_create_csr(rp, ci2, va)
+
+
+# ------------------------------------------- generalized averaged quadrature
+
+@pytest.mark.parametrize("prec", [evc.EVC_FP64, evc.EVC_MIXED])
+def test_ga_quadrature_matches_oracle(prec):
+    # Sec. 3.4: the same Lanczos steps, step 5 of Algorithm 2 on the extended
+    # tridiagonal of Eq. GA_Tk.
+    N, h = 12, 0.3
+    V = I.gaussian_wells(N, h, nwells=6, seed=1)
+    shifts = [-2.5, 0.5]
+    m, k = 40, 10
+    with evc.Context.stencil(N, h, 2, V, precision=prec) as ctx:
+        ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, 8, 1.0)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_QUADRATURE, evc.EVC_QUAD_GA)
+        L, q, st = ctx.count_slices(shifts, m, k)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_QUADRATURE, evc.EVC_QUAD_GAUSS)
+        Lg, qg, _ = ctx.count_slices(shifts, m, k)
+    P = O.Problem.stencil(N, h, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
+    qr, sr, Lr = O.count(P, shifts, m, k, seed=0, rule=1)
+    qgr, _, _ = O.count(P, shifts, m, k, seed=0, rule=0)
+    if prec == evc.EVC_FP64:
+        assert np.max(np.abs(q - qr)) < FP64_TOL
+        assert np.max(np.abs(qg - qgr)) < FP64_TOL
+    assert np.max(np.abs(L - Lr)) < MIXED_EST_TOL
+    assert np.max(np.abs(q - qg)) > 1e-6      # the two rules differ at k = 10
+
+
+def test_ga_adaptive_csr_fp64():
+    csr = I.laplace2d_dirichlet(20)
+    shifts = [0.5, 1.5, 3.0]
+    with evc.Context.csr(csr, precision=evc.EVC_FP64) as ctx:
+        ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_QUADRATURE, evc.EVC_QUAD_GA)
+        L, q, st = ctx.count_slices(shifts, 12, 40, tol=0.25)
+    P = O.Problem.csr_matrix(csr, O.PREC_JACOBI)
+    qr, sr, Lr = O.count(P, shifts, 12, 40, tol=0.25, seed=0, rule=1)
+    assert list(st) == list(sr)
+    assert np.max(np.abs(q - qr)) < FP64_TOL

@@ -399,3 +399,44 @@ def test_paper_table1_laplace_unpreconditioned():
     se = quad[0].std(ddof=1) / np.sqrt(g["m"])
     err = abs(L[0] - g["exact_negative_inertia"])
     assert err < max(4 * se, g["relative_error_reported"] * g["exact_negative_inertia"]) + 4 * se
+
+
+# --------------------------------------------------- generalized averaged
+
+def test_ga_quadrature_exact_to_degree_2k():
+    # Sec. 3.4: the generalized averaged rule from k Lanczos steps is exact for
+    # polynomials of degree 2k (Gauss: 2k-1).  The moments of the extended
+    # (2k-1)-order tridiagonal match v^T C^j v up to j = 2k.
+    A = I.random_symmetric_dense(25, seed=8)
+    P = O.Problem.dense_matrix(A, O.PREC_JACOBI)
+    tau = -0.1
+    v = O.probe_vector(1, 2, 25)
+    Cm = _dense_C(P, tau)
+    for k in (2, 3, 5):
+        al, be, _, _ = O.lanczos(P, tau, v, k + 1)
+        al, be = al[:k], be[:k + 1]
+        d = np.concatenate([al, al[:-1][::-1]])
+        off = np.concatenate([be[1:k], [be[k]], be[1:k - 1][::-1]])
+        J = np.diag(d) + np.diag(off, 1) + np.diag(off, -1)
+        for j in range(0, 2 * k + 1):
+            lhs = 25.0 * np.linalg.matrix_power(J, j)[0, 0]
+            rhs = v @ np.linalg.matrix_power(Cm, j) @ v
+            assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-9)
+        lhs = 25.0 * np.linalg.matrix_power(J, 2 * k + 1)[0, 0]
+        rhs = v @ np.linalg.matrix_power(Cm, 2 * k + 1) @ v
+        assert abs(lhs - rhs) > 1e-6 * abs(rhs)
+        # the oracle's GA quadrature is the step-function rule of exactly this matrix
+        w, Z = np.linalg.eigh(J)
+        assert O.ga_quad(al, be, 25.0) == pytest.approx(25.0 * np.sum(Z[0, w < 0] ** 2), abs=1e-10)
+
+
+def test_ga_equals_gauss_after_breakdown_and_at_k1():
+    distinct = [-2.0, -0.5, 0.7, 1.5, 3.0]
+    A = I.random_symmetric_dense(30, seed=4, distinct=distinct)
+    P = O.Problem.dense_matrix(A)
+    v = O.probe_vector(9, 1, 30)
+    al, be, _, kd = O.lanczos(P, 0.0, v, 12)
+    assert kd == 5
+    assert O.ga_quad(al, be, 30.0) == pytest.approx(O.gauss_quad(al, be, 30.0), abs=1e-9)
+    al1, be1, _, _ = O.lanczos(P, 0.0, v, 1)
+    assert O.ga_quad(al1, be1, 30.0) == O.gauss_quad(al1, be1, 30.0)
