@@ -102,30 +102,39 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
     kind = {"identity": evc.EVC_PREC_IDENTITY, "jacobi": evc.EVC_PREC_JACOBI,
             "cheb": evc.EVC_PREC_CHEB_KINETIC}[W.precond]
     ctx.set_precond(kind, *W.prec_params)
+    evc.evc_set_option(ctx.h, evc.EVC_OPT_MIN_STEPS, W.min_steps)
     ctx.reserve(len(W.shifts), W.nprobe, W.maxsteps)
     return ctx
 
 
-def _stencil_roofline(evc, recs, peak, peak_kind):
-    st = [r for r in recs if r[0] == evc.EVC_K_STENCIL and r[2] > 0]
-    if not st:
-        return None, {}
-    ms = np.array([r[2] for r in st])
-    by = np.array([r[3] for r in st])
-    ach = by.sum() / (ms.sum() * 1e-3) / 1e9            # GB/s over all stencil passes
+def _roofline(evc, recs, peak, peak_kind):
+    """Roofline of the kernel class with the largest device time in the launch
+    list: achieved = sum of its launches' algorithmic bytes / sum of their
+    CUDA-event durations."""
     per_kind = {}
+    best = None
     for k, name in enumerate(evc.KERNEL_NAMES):
         rr = [r for r in recs if r[0] == k and r[2] > 0]
-        if rr:
-            t = sum(r[2] for r in rr)
-            b = sum(r[3] for r in rr)
-            per_kind[name] = {"launches": len(rr), "ms": round(t, 4),
-                              "GB/s": round(b / (t * 1e-3) / 1e9, 1) if t > 0 else None}
-    roof = {"bound": "hbm", "kernel": "stencil_pass_kernel", "achieved": round(ach, 1),
-            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "peak_source": peak_kind, "traffic": None,
-            "bytes_per_launch_avg": float(by.mean()), "ms_per_launch_avg": float(ms.mean()),
-            "launches": len(st)}
+        if not rr:
+            continue
+        t = sum(r[2] for r in rr)
+        b = sum(r[3] for r in rr)
+        per_kind[name] = {"launches": len(rr), "ms": round(t, 4),
+                          "GB/s": round(b / (t * 1e-3) / 1e9, 1) if t > 0 else None}
+        if best is None or t > best[1]:
+            best = (name, t, b, len(rr))
+    if best is None:
+        return None, per_kind
+    name, t, b, cnt = best
+    kernel = {"stencil": "stencil_pass_kernel", "csr": "csr_pass_kernel",
+              "dots": "reorth_dots_kernel", "update": "reorth_update_kernel"}.get(name, name)
+    ach = b / (t * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": kernel, "achieved": round(ach, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
+            "traffic": None, "bytes_per_launch_avg": b / cnt, "ms_per_launch_avg": t / cnt,
+            "launches": cnt, "share_of_step": None}
+    tot = sum(v["ms"] for v in per_kind.values())
+    roof["share_of_step"] = round(t / tot, 3) if tot > 0 else None
     return roof, per_kind
 
 
@@ -179,13 +188,14 @@ def run_ours(args):
 
     # ---- headline: FP32-mixed, inputs resident
     ctx = _make_ctx(evc, W, evc.EVC_MIXED, sp)
+    ws_mixed = evc.evc_workspace_bytes(ctx.h, S, m, k)
     clocks = ClockSampler(local)
     clocks.start()
     ms_mixed, L_mixed, steps_mixed = timed(ctx, args.steps, args.warmup, profile=True)
     clk = clocks.stop()
     recs = evc.evc_get_profile(ctx.h)
     launches_per_step = len(recs)
-    roof, per_kind = _stencil_roofline(evc, recs, peak, peak_kind)
+    roof, per_kind = _roofline(evc, recs, peak, peak_kind)
     # ---- e2e: host V (pinned) -> device, count, per-probe results -> host
     Vh = torch.from_numpy(W.potential().astype(np.float32)).pin_memory() if W.kind == "stencil" else None
     evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
@@ -204,14 +214,22 @@ def run_ours(args):
     h2d = W.n * 4 if Vh is not None else 0
     d2h = S * m * 8 + S * 8 + S * 4
     ctx.close()
+    torch.cuda.empty_cache()
     # ---- FP64 path on the same GPU
-    ms_fp64, L_fp64 = None, None
+    ms_fp64, L_fp64, fp64_note = None, None, None
     if not args.skip_fp64:
-        ctx64 = _make_ctx(evc, W, evc.EVC_FP64, sp)
-        ms_fp64, L_fp64, steps_fp64 = timed(ctx64, max(1, args.steps // 2), 1, profile=False)
-        ctx64.close()
+        free, _ = torch.cuda.mem_get_info()
+        need = 2 * ws_mixed
+        if need > 0.9 * free:
+            fp64_note = f"FP64 workspace {need / 1e9:.0f} GB does not fit next to the rest"
+        else:
+            ctx64 = _make_ctx(evc, W, evc.EVC_FP64, sp)
+            ms_fp64, L_fp64, steps_fp64 = timed(ctx64, max(1, args.steps // 2), 1, profile=False)
+            psteps64 = float(m * int(np.sum(steps_fp64)))
+            ctx64.close()
 
-    psteps = float(S * m * k)          # probe-steps per count (tol = 0: all columns run k steps)
+    # probe-steps per count: every probe of a shift runs that shift's steps
+    psteps = float(m * int(np.sum(steps_mixed)))
     t_step = ms_mixed / args.steps
     t_max = t_step
     e2e_t = (t_e2e / args.steps) if t_e2e is not None else float("nan")
@@ -220,8 +238,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max, e2e_t = float(t[0]), float(t[1])
     value = world * psteps / (t_max * 1e-3)
-    est_mixed = float(L_mixed[1] - L_mixed[0]) if S == 2 else None
-    est_fp64 = float(L_fp64[1] - L_fp64[0]) if (S == 2 and L_fp64 is not None) else None
+    est_mixed = float(L_mixed[-1] - L_mixed[0])
+    est_fp64 = float(L_fp64[-1] - L_fp64[0]) if L_fp64 is not None else None
     fp64_steps = max(1, args.steps // 2)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -229,10 +247,13 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": W.name, "n": W.n, "shifts": S, "probes_per_shift": m,
-                   "lanczos_steps": k, "precond": "chebyshev-8 kinetic (c=1)",
+                   "lanczos_steps_max": k, "tol": W.tol,
+                   "steps_used": [int(x) for x in steps_mixed],
+                   "precond": {"cheb": f"chebyshev-{int(W.prec_params[0])} kinetic (c={W.prec_params[1]})",
+                               "jacobi": "jacobi (eps 1e-3)", "identity": "none"}[W.precond],
                    "precision": "FP32 vectors/operator, FP64 alpha/beta/reorth coefficients/eig",
-                   "step": "one full count: all shifts x probes x Lanczos steps",
-                   "l2": "inputs larger than L2 (Lanczos basis 4.2 GB streamed every step)",
+                   "step": "one full count: all shifts x probes x executed Lanczos steps",
+                   "l2": f"inputs larger than L2 (Lanczos basis {ws_mixed / 1e9:.1f} GB workspace streamed every step)",
                    "parallelism": f"replicas{world}"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
@@ -241,13 +262,13 @@ def run_ours(args):
         "e2e": {"value": round(world * psteps / e2e_t, 1) if t_e2e is not None else None, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "evc_set_values(V from pinned host) + evc_count_slices (host outputs)"},
-        "fp64": None if ms_fp64 is None else {
-            "value": round(world * psteps / (ms_fp64 / fp64_steps * 1e-3), 1), "unit": UNIT,
+        "fp64": {"skipped": fp64_note or "--skip-fp64"} if ms_fp64 is None else {
+            "value": round(world * psteps64 / (ms_fp64 / fp64_steps * 1e-3), 1), "unit": UNIT,
             "ms_per_step": round(ms_fp64 / fp64_steps, 3)},
         "estimate": {"mixed": est_mixed, "fp64": est_fp64,
                      "mixed_minus_fp64": (est_mixed - est_fp64) if est_fp64 is not None else None,
-                     "n_below_mixed": [float(x) for x in L_mixed],
-                     "n_below_fp64": None if L_fp64 is None else [float(x) for x in L_fp64]},
+                     "n_below_mixed": [round(float(x), 4) for x in L_mixed],
+                     "n_below_fp64": None if L_fp64 is None else [round(float(x), 4) for x in L_fp64]},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_probes, seed=args.seed)

@@ -138,8 +138,9 @@ int evc_set_workspace(evc_ctx* ctx, void* dptr, size_t bytes);
  * [xi, eta] (xi < eta).
  *   nprobe      : m >= 1 probes (ids 0..m-1), the same for both shifts.
  *   maxsteps    : k, 1..EVC_MAX_STEPS, clamped to n.
- *   tol         : <= 0 runs exactly k steps; > 0 stops a shift after the
- *                 first step i >= 2 with |L(i) - L(i-1)| <= tol.
+ *   tol         : <= 0 runs exactly k steps; > 0 stops a shift at the first
+ *                 step i >= max(3, EVC_OPT_MIN_STEPS) with
+ *                 |L(i) - L(i-1)| <= tol and |L(i-1) - L(i-2)| <= tol.
  *   estimate    : L_eta - L_xi (real; the paper's count is its rounding).
  *   per_probe_quad (may be NULL): double[2*nprobe], [0..m) for xi, [m..2m) eta.
  *   steps_used  (may be NULL): int[2].
@@ -189,8 +190,10 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       the (2k-1)-order extension of J_k built by mirroring
  *                       its coefficients around beta_{k+1} (Sec. 3.4,
  *                       Eq. GA_Tk).  Same Lanczos steps, different step 5 of
- *                       Algorithm 2.                                          */
-enum { EVC_OPT_GRAPH = 1, EVC_OPT_PROFILE = 2, EVC_OPT_QUADRATURE = 3 };
+ *                       Algorithm 2.
+ *   EVC_OPT_MIN_STEPS : under a tolerance (tol > 0), no shift stops before
+ *                       this step (default 3, at least 3).                   */
+enum { EVC_OPT_GRAPH = 1, EVC_OPT_PROFILE = 2, EVC_OPT_QUADRATURE = 3, EVC_OPT_MIN_STEPS = 4 };
 enum { EVC_QUAD_GAUSS = 0, EVC_QUAD_GA = 1 };
 int evc_set_option(evc_ctx* ctx, int option, int64_t value);
 

@@ -392,7 +392,7 @@ double evo_ga_quad(int k, const double* alpha, const double* beta, double vnorm2
 
 int evo_count_rule(const evo_problem* P, const double* shifts, int S, int m,
                    const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
-                   double breakdown_rel, int nthreads, int rule,
+                   double breakdown_rel, int nthreads, int rule, int min_steps,
                    double* quad, int* steps, double* L)
 {
     const int64_t n = P->n;
@@ -433,12 +433,18 @@ int evo_count_rule(const evo_problem* P, const double* shifts, int S, int m,
     for (int s = 0; s < S; ++s) {
         int ks = kmax;
         if (tol > 0.0) {
-            double prev = 0.0;
+            /* stop at the first step i >= max(3, min_steps) where L changed by
+             * at most tol over each of the last two steps */
+            double prev = 0.0, prev2 = 0.0;
             for (int i = 1; i <= kmax; ++i) {
                 double Li = 0.0;
                 for (int j = 0; j < m; ++j) Li += quad_hist[(size_t)(s * m + j) * kmax + (i - 1)];
                 Li /= m;
-                if (i >= 2 && fabs(Li - prev) <= tol) { ks = i; break; }
+                if (i >= 3 && i >= min_steps && fabs(Li - prev) <= tol && fabs(prev - prev2) <= tol) {
+                    ks = i;
+                    break;
+                }
+                prev2 = prev;
                 prev = Li;
             }
         }
@@ -460,5 +466,5 @@ int evo_count(const evo_problem* P, const double* shifts, int S, int m,
               double* quad, int* steps, double* L)
 {
     return evo_count_rule(P, shifts, S, m, probe_ids, kmax, tol, seed, breakdown_rel, nthreads, 0,
-                          quad, steps, L);
+                          3, quad, steps, L);
 }

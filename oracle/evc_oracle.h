@@ -98,19 +98,20 @@ double evo_ga_quad(int k, const double* alpha, const double* beta, double vnorm2
 /* The estimator L_tau(k, m) for S shifts with m probes each.
  * Column (s, j) uses probe id probe_ids[j] (or j if probe_ids is NULL) and the
  * seeded Rademacher probe above; the same probes serve every shift.
- * tol <= 0: every shift runs kmax steps. tol > 0: shift s stops after the
- * first step i >= 2 with |L_s(i) - L_s(i-1)| <= tol (kmax caps it).
+ * tol <= 0: every shift runs kmax steps. tol > 0: shift s stops at the first
+ * step i >= 3 with |L_s(i) - L_s(i-1)| <= tol and |L_s(i-1) - L_s(i-2)| <= tol
+ * (kmax caps it).
  * Outputs: quad[s*m + j], steps[s], L[s] (= mean_j quad[s*m + j]).
  * nthreads <= 0: OpenMP default. */
 int evo_count(const evo_problem* P, const double* shifts, int S, int m,
               const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
               double breakdown_rel, int nthreads,
               double* quad, int* steps, double* L);
-/* Same with the quadrature rule chosen: rule 0 = Gauss, 1 = generalized
- * averaged Gauss. */
+/* Same with the quadrature rule chosen (rule 0 = Gauss, 1 = generalized
+ * averaged Gauss) and no tolerance stop before step max(3, min_steps). */
 int evo_count_rule(const evo_problem* P, const double* shifts, int S, int m,
                    const int64_t* probe_ids, int kmax, double tol, uint64_t seed,
-                   double breakdown_rel, int nthreads, int rule,
+                   double breakdown_rel, int nthreads, int rule, int min_steps,
                    double* quad, int* steps, double* L);
 
 #ifdef __cplusplus

@@ -84,7 +84,7 @@ def _load():
                                       C.POINTER(C.c_int), d]
             lib.evo_count_rule.argtypes = [P, d, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                            C.c_double, C.c_uint64, C.c_double, C.c_int, C.c_int,
-                                           d, C.POINTER(C.c_int), d]
+                                           C.c_int, d, C.POINTER(C.c_int), d]
             lib.evo_ga_quad.restype = C.c_double
             lib.evo_ga_quad.argtypes = [C.c_int, d, d, C.c_double]
             _lib = lib
@@ -230,7 +230,7 @@ def ga_quad(alpha, beta, vnorm2):
 
 
 def count(P: Problem, shifts, m, kmax, tol=0.0, seed=0, probe_ids=None,
-          breakdown_rel=BREAKDOWN_REL, nthreads=0, rule=0):
+          breakdown_rel=BREAKDOWN_REL, nthreads=0, rule=0, min_steps=3):
     """Algorithm 2 for every shift: returns (quad[S, m], steps[S], L[S]).
 
     rule 0: Gauss quadrature (Eq. gauss_quad); 1: generalized averaged Gauss
@@ -246,7 +246,8 @@ def count(P: Problem, shifts, m, kmax, tol=0.0, seed=0, probe_ids=None,
         assert pid.size == m
     rc = _load().evo_count_rule(P.ref, _dp(shifts), S, m,
                                 pid.ctypes.data if pid is not None else None, kmax, tol,
-                                C.c_uint64(seed), breakdown_rel, nthreads, int(rule), _dp(quad),
+                                C.c_uint64(seed), breakdown_rel, nthreads, int(rule),
+                                int(min_steps), _dp(quad),
                                 steps.ctypes.data_as(C.POINTER(C.c_int)), _dp(L))
     assert rc == 0, rc
     return quad.reshape(S, m), steps, L

@@ -56,6 +56,7 @@ struct evc_ctx {
     void* own_col = nullptr;
     void* own_val = nullptr;
     double* own_diag = nullptr;
+    int32_t* own_perm = nullptr;
     // stencil
     StencilOp sten{};
     void* own_V = nullptr;
@@ -68,6 +69,7 @@ struct evc_ctx {
     std::vector<double> cheb_coef;
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
+    int min_steps = 3;
     // workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -80,7 +82,8 @@ struct evc_ctx {
     cudaEvent_t param_ev = nullptr;
     // launch list of the enqueued sequence (with timing events when profiling)
     bool profile = false;
-    struct Rec { int kind, step; double bytes; cudaEvent_t e0, e1; };
+    // bytes of a launch = fixed + per_chunk * (chunks active in that step)
+    struct Rec { int kind, step; double fixed, per_chunk; cudaEvent_t e0, e1; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -180,11 +183,13 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.kdone = I(ncol);
     r.shifts = D(S);
     r.Lprev = D(S);
+    r.Lprev2 = D(S);
     r.Lfinal = D(S);
     r.steps = I(S);
     r.sdone = I(S);
     r.chunk_active = I(nchunk);
     r.cnt_upd = I(nchunk);
+    r.nactive = I(kmax + 1);
     r.part_dot = D((size_t)nchunk * nblk * kmax * CW);
     r.part_gram = D((size_t)nchunk * nblk * kmax * CW);
     r.hbuf = D((size_t)kmax * ncol);
@@ -195,6 +200,7 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.tol = D(1);
     r.breakdown_rel = c->precision == EVC_FP64 ? 1e-12 : 1e-6;
     r.ga = c->quad_rule == EVC_QUAD_GA ? 1 : 0;
+    r.min_steps = c->min_steps;
     return off;
 }
 
@@ -325,9 +331,9 @@ cudaEvent_t pool_event(evc_ctx* ctx)
 
 // Enqueue one kernel launch, bracketed by timing events when profiling.
 template <class F>
-int rec(evc_ctx* ctx, int kind, int step, double bytes, F&& launch)
+int rec(evc_ctx* ctx, int kind, int step, double fixed, double per_chunk, F&& launch)
 {
-    evc_ctx::Rec r{kind, step, bytes, nullptr, nullptr};
+    evc_ctx::Rec r{kind, step, fixed, per_chunk, nullptr, nullptr};
     if (ctx->profile) {
         r.e0 = pool_event(ctx);
         r.e1 = pool_event(ctx);
@@ -352,19 +358,15 @@ struct BTerm {
 };
 
 template <typename T>
-double stencil_bytes(const evc_ctx* ctx, const Run& r, const StencilPass& p, bool jac)
-{
-    const double vec = (double)r.nchunk * r.n * CW * sizeof(T);
-    double b = vec * (2 + (p.x ? 1 : 0) + (p.prev ? 1 : 0) + (p.pp ? 1 : 0));
-    if (p.useV) b += (double)r.n * sizeof(T);
-    if (jac) b += (double)r.S * r.n * sizeof(T);
-    return b;
-}
-
-template <typename T>
 int stencil(evc_ctx* ctx, const Run& r, int step, const StencilPass& p, bool jac)
 {
-    return rec(ctx, EVC_K_STENCIL, step, stencil_bytes<T>(ctx, r, p, jac),
+    // compulsory traffic: the stencil operand and every pointwise operand read
+    // once, the output written once (per active chunk); V and Jacobi scales once
+    const double vchunk = (double)r.n * CW * sizeof(T);
+    const double per = vchunk * (2 + (p.x ? 1 : 0) + (p.prev ? 1 : 0) + (p.pp ? 1 : 0));
+    double fixed = p.useV ? (double)r.n * sizeof(T) : 0.0;
+    if (jac) fixed += (double)r.S * r.n * sizeof(T);
+    return rec(ctx, EVC_K_STENCIL, step, fixed, per,
                [&] { return launch_stencil_pass<T>(ctx->sten, r, p, jac, ctx->stream); });
 }
 
@@ -446,13 +448,13 @@ template <typename T>
 int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
 {
     cudaStream_t st = ctx->stream;
-    const double vec = (double)r.nchunk * r.n * CW * sizeof(T);
+    const double vchunk = (double)r.n * CW * sizeof(T);
     const double colb = (double)r.ncol * 8;
-    int rc = rec(ctx, EVC_K_INIT, 0, colb * 8, [&] { return launch_init_state(r, st); });
-    if (!rc) rc = rec(ctx, EVC_K_INIT, 0, vec, [&] { return launch_init_probe<T>(r, st); });
+    int rc = rec(ctx, EVC_K_INIT, 0, colb * 8, 0.0, [&] { return launch_init_state(r, st); });
+    if (!rc) rc = rec(ctx, EVC_K_INIT, 0, 0.0, vchunk, [&] { return launch_init_probe<T>(r, st); });
     if (!rc && uses_jac(ctx)) {
         const double vdiag = ctx->op == OP_STENCIL ? ctx->sten.cd : 0.0;
-        rc = rec(ctx, EVC_K_JACOBI, 0, (double)r.S * r.n * sizeof(T) + r.n * 8.0, [&] {
+        rc = rec(ctx, EVC_K_JACOBI, 0, (double)r.S * r.n * sizeof(T) + r.n * 8.0, 0.0, [&] {
             return launch_jacobi_scales<T>(r, ctx->op == OP_CSR ? ctx->csr.diag : nullptr,
                                            ctx->op == OP_STENCIL ? ctx->sten.V : nullptr, vdiag,
                                            ctx->jac_eps, st);
@@ -467,10 +469,12 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         T* wout = basis + (int64_t)i * r.slot_stride;
         const double* si = r.scl + (int64_t)(i - 1) * r.ncol;
         if (ctx->op == OP_CSR) {
-            const double ab = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1);
-            const double b = ab + vec * (2 + (qprev ? 1 : 0)) +
-                             (uses_jac(ctx) ? (double)r.S * r.n * sizeof(T) : 0.0);
-            rc = rec(ctx, EVC_K_CSR, i, b,
+            // the CSR structure and values once; per chunk, one gathered 32-column
+            // x row per stored entry, the output and q_{i-1}
+            const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
+                                 (uses_jac(ctx) ? (double)r.S * r.n * sizeof(T) : 0.0);
+            const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk * (1 + (qprev ? 1 : 0));
+            rc = rec(ctx, EVC_K_CSR, i, fixed, per,
                      [&] { return launch_csr_pass<T>(ctx->csr, r, i, uses_jac(ctx), st); });
         } else if (ctx->prec == EVC_PREC_CHEB_KINETIC) {
             T* W0 = static_cast<T*>(work);
@@ -510,20 +514,22 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             rc = stencil<T>(ctx, r, i, p, uses_jac(ctx));
         }
         if (rc) return rc;
-        rc = rec(ctx, EVC_K_DOTS, i, vec * (i + 1), [&] { return launch_dots<T>(r, i, st); });
+        rc = rec(ctx, EVC_K_DOTS, i, 0.0, vchunk * (i + 1), [&] { return launch_dots<T>(r, i, st); });
         if (!rc)
-            rc = rec(ctx, EVC_K_REDUCE, i, 2.0 * r.nchunk * r.nblk * i * CW * 8 + colb * 3 * i,
+            rc = rec(ctx, EVC_K_REDUCE, i, colb * 3 * i, 2.0 * r.nblk * i * CW * 8,
                      [&] { return launch_reduce(r, i, st); });
         if (!rc)
-            rc = rec(ctx, EVC_K_REDUCE, i, colb * (2.0 * i + i * (i + 1) / 2),
+            rc = rec(ctx, EVC_K_REDUCE, i, colb * (2.0 * i + i * (i + 1) / 2), 0.0,
                      [&] { return launch_coef(r, i, st); });
         if (!rc)
-            rc = rec(ctx, EVC_K_UPDATE, i, vec * (i + 2), [&] { return launch_update<T>(r, i, st); });
+            rc = rec(ctx, EVC_K_UPDATE, i, 0.0, vchunk * (i + 2),
+                     [&] { return launch_update<T>(r, i, st); });
         const bool last = (i == r.kmax);
         if (!rc && (adaptive || last))
-            rc = rec(ctx, EVC_K_FINISH, i, colb * (2.0 * i + 2),
+            rc = rec(ctx, EVC_K_FINISH, i, colb * (2.0 * i + 2), 0.0,
                      [&] { return launch_finish(r, i, last, st); });
-        if (!rc && adaptive) rc = rec(ctx, EVC_K_FINISH, i, colb, [&] { return launch_active(r, st); });
+        if (!rc && adaptive)
+            rc = rec(ctx, EVC_K_FINISH, i, colb, 0.0, [&] { return launch_active(r, i, st); });
     }
     return rc;
 }
@@ -813,7 +819,28 @@ int evc_create_csr(const evc_csr* A, int precision, void* stream, evc_ctx** out)
         A->on_device ? A->val_is_fp32 : (ctx->tsize == 4), ctx->own_diag, n);
     if (cudaGetLastError() != cudaSuccess) return cleanup(EVC_ECUDA);
     ctx->csr.diag = ctx->own_diag;
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(EVC_ECUDA);
+    // visit order of the rows: by decreasing length, so the rows that share a
+    // warp in the operator kernel have similar lengths
+    {
+        std::vector<int64_t> rp((size_t)n + 1);
+        if (A->on_device) {
+            if (cudaMemcpy(rp.data(), A->row_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return cleanup(EVC_ECUDA);
+        } else {
+            memcpy(rp.data(), A->row_ptr, (n + 1) * 8);
+        }
+        std::vector<int32_t> perm((size_t)n);
+        for (int64_t r = 0; r < n; ++r) perm[r] = (int32_t)r;
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+            return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+        });
+        if (dmalloc(reinterpret_cast<void**>(&ctx->own_perm), n * 4)) return cleanup(EVC_ENOMEM);
+        if (cudaMemcpyAsync(ctx->own_perm, perm.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess)
+            return cleanup(EVC_ECUDA);
+        ctx->csr.perm = ctx->own_perm;
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(EVC_ECUDA);
+    }
     *out = ctx;
     return EVC_OK;
 }
@@ -1056,6 +1083,14 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         drop_graph(ctx);
         return EVC_OK;
     }
+    if (option == EVC_OPT_MIN_STEPS) {
+        if (value < 1 || value > EVC_MAX_STEPS)
+            return fail(ctx, EVC_EINVAL, "min steps must be in [1, %d]", EVC_MAX_STEPS);
+        ctx->min_steps = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
     if (option == EVC_OPT_QUADRATURE) {
         if (value != EVC_QUAD_GAUSS && value != EVC_QUAD_GA)
             return fail(ctx, EVC_EINVAL, "unknown quadrature rule %lld", (long long)value);
@@ -1073,12 +1108,21 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec)
     if (nrec) *nrec = (int)ctx->recs.size();
     if (!recs || cap <= 0) return EVC_OK;
     CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<int> nact;
+    if (ctx->have_run) {
+        nact.resize(ctx->run.kmax + 1);
+        CU(cudaMemcpy(nact.data(), ctx->run.nactive, nact.size() * sizeof(int),
+                      cudaMemcpyDeviceToHost));
+    }
     const int cnt = std::min<int>(cap, (int)ctx->recs.size());
     for (int i = 0; i < cnt; ++i) {
         const evc_ctx::Rec& r = ctx->recs[i];
         recs[i].kind = r.kind;
         recs[i].step = r.step;
-        recs[i].bytes = r.bytes;
+        const int act = (ctx->have_run && r.step >= 1 && r.step <= (int)nact.size())
+                            ? nact[r.step - 1]
+                            : (ctx->have_run ? ctx->run.nchunk : 0);
+        recs[i].bytes = r.fixed + r.per_chunk * act;
         float ms = -1.0f;
         if (r.e0 && r.e1) CU(cudaEventElapsedTime(&ms, r.e0, r.e1));
         recs[i].ms = ms;
@@ -1102,6 +1146,7 @@ void evc_destroy(evc_ctx* ctx)
     if (ctx->own_col) cudaFree(ctx->own_col);
     if (ctx->own_val) cudaFree(ctx->own_val);
     if (ctx->own_diag) cudaFree(ctx->own_diag);
+    if (ctx->own_perm) cudaFree(ctx->own_perm);
     if (ctx->own_V) cudaFree(ctx->own_V);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->pinres) cudaFreeHost(ctx->pinres);

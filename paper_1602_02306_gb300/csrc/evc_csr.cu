@@ -3,11 +3,11 @@
 // line of the loop body), with M = I or the Jacobi scaling
 // M = diag((|a_rr - sigma| + eps)^(-1/2)) fused as row and column scales.
 //
-// One warp owns one row of one 32-column chunk: lanes are the probe columns,
-// so every gathered x row is one contiguous 128-byte (FP32) / 256-byte
-// (FP64) segment, and the row's (col, val) pairs are read once per chunk and
-// broadcast through warp shuffles.  q_i = s_i P_i is scaled on the fly.
+// Every gathered x row of a chunk is one contiguous 128-byte (FP32) / 256-byte
+// (FP64) segment; q_i = s_i P_i is scaled on the fly.
 #include "evc_internal.cuh"
+
+#include <cstring>
 
 namespace evc {
 namespace {
@@ -26,63 +26,115 @@ struct CArgs {
     const int* chunk_active;
 };
 
+template <typename T> struct alignas(16) Pack { T v[16 / sizeof(T)]; };
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; };
+template <> struct Vec16<double> { typedef double2 type; };
+
+template <typename T>
+__device__ __forceinline__ Pack<T> ldg16(const T* p)
+{
+    typename Vec16<T>::type t = __ldg(reinterpret_cast<const typename Vec16<T>::type*>(p));
+    Pack<T> r;
+    memcpy(&r, &t, 16);
+    return r;
+}
+
+// A group of LPR = CW / W lanes owns one row of one chunk; each lane holds W
+// consecutive columns (one 16-byte vector), so one gather instruction of the
+// warp fetches 32/LPR whole x rows.  Rows are visited in the order of
+// op.perm (rows sorted by length, longest first) so the rows sharing a warp
+// have similar lengths; each group broadcasts the row's (col, val) pairs from
+// its own lanes with warp shuffles.
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(kThreads)
 csr_pass_kernel(CArgs a)
 {
+    constexpr int W = 16 / sizeof(T);
+    constexpr int LPR = CW / W;                 // lanes per row
+    constexpr int RPW = 32 / LPR;               // rows per warp
     const int ch = blockIdx.y;
     if (!a.chunk_active[ch]) return;
     const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    if (row >= a.op.n) return;
-    const int c = ch * CW + lane;
+    const int grp = lane / LPR, sub = lane % LPR;
+    const int64_t slotrow = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * RPW + grp;
     const int64_t n = a.op.n;
+    const bool valid = slotrow < n;
+    const int64_t row = valid ? (a.op.perm ? (int64_t)a.op.perm[slotrow] : slotrow) : 0;
+    const int c0 = ch * CW + sub * W;
     const T* x = static_cast<const T*>(a.x) + ch * a.chunk_stride;
     const T* val = static_cast<const T*>(a.op.val);
-    const T* jr = JAC ? static_cast<const T*>(a.jac) + (int64_t)a.shift_of[c] * n : nullptr;
+    const T* jr[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        jr[w] = JAC ? static_cast<const T*>(a.jac) + (int64_t)a.shift_of[c0 + w] * n : nullptr;
 
-    const int64_t beg = a.op.row_ptr[row], end = a.op.row_ptr[row + 1];
-    T acc0 = 0, acc1 = 0;
-    for (int64_t k0 = beg; k0 < end; k0 += 32) {
-        const int64_t kk = k0 + lane;
-        int mycol = 0;
+    const int64_t beg = valid ? a.op.row_ptr[row] : 0, end = valid ? a.op.row_ptr[row + 1] : 0;
+    // the warp walks the longest of its rows; shorter rows contribute zeros
+    int64_t len = end - beg, mx = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (int64_t)__shfl_xor_sync(0xffffffffu, mx, o));
+    T acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = 0;
+    for (int64_t k0 = 0; k0 < mx; k0 += LPR) {
+        const int64_t kk = beg + k0 + sub;
+        int mycol = (int)row;
         T myval = 0;
-        if (kk < end) {
+        if (k0 + sub < len) {
             mycol = __ldg(a.op.col + kk);
             myval = __ldg(val + kk);
         }
-        const int cnt = (int)min((int64_t)32, end - k0);
+        const int cnt = (int)min((int64_t)LPR, mx - k0);
         int t = 0;
         for (; t + 1 < cnt; t += 2) {
-            const int ca = __shfl_sync(0xffffffffu, mycol, t);
-            const int cb = __shfl_sync(0xffffffffu, mycol, t + 1);
-            const T va = __shfl_sync(0xffffffffu, myval, t);
-            const T vb = __shfl_sync(0xffffffffu, myval, t + 1);
-            T xa = __ldg(x + (int64_t)ca * CW + lane);
-            T xb = __ldg(x + (int64_t)cb * CW + lane);
-            if (JAC) { xa *= __ldg(jr + ca); xb *= __ldg(jr + cb); }
-            acc0 += va * xa;
-            acc1 += vb * xb;
+            const int ca = __shfl_sync(0xffffffffu, mycol, grp * LPR + t);
+            const int cb = __shfl_sync(0xffffffffu, mycol, grp * LPR + t + 1);
+            const T va = __shfl_sync(0xffffffffu, myval, grp * LPR + t);
+            const T vb = __shfl_sync(0xffffffffu, myval, grp * LPR + t + 1);
+            Pack<T> xa = ldg16(x + (int64_t)ca * CW + sub * W);
+            Pack<T> xb = ldg16(x + (int64_t)cb * CW + sub * W);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                T sa = xa.v[w], sb = xb.v[w];
+                if (JAC) { sa *= __ldg(jr[w] + ca); sb *= __ldg(jr[w] + cb); }
+                acc[w] += va * sa + vb * sb;
+            }
         }
         if (t < cnt) {
-            const int ca = __shfl_sync(0xffffffffu, mycol, t);
-            const T va = __shfl_sync(0xffffffffu, myval, t);
-            T xa = __ldg(x + (int64_t)ca * CW + lane);
-            if (JAC) xa *= __ldg(jr + ca);
-            acc0 += va * xa;
+            const int ca = __shfl_sync(0xffffffffu, mycol, grp * LPR + t);
+            const T va = __shfl_sync(0xffffffffu, myval, grp * LPR + t);
+            Pack<T> xa = ldg16(x + (int64_t)ca * CW + sub * W);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                T sa = xa.v[w];
+                if (JAC) sa *= __ldg(jr[w] + ca);
+                acc[w] += va * sa;
+            }
         }
     }
-    T center = __ldg(x + row * CW + lane);
-    T mr = 1;
-    if (JAC) { mr = __ldg(jr + row); center *= mr; }
-    T res = (acc0 + acc1) - (T)a.sigma[c] * center;
-    if (JAC) res *= mr;
-    res *= (T)a.insc[c];
-    if (a.pp) {
-        const T* pp = static_cast<const T*>(a.pp) + ch * a.chunk_stride;
-        res -= (T)a.ppc[c] * pp[row * CW + lane];
+    if (!valid) return;
+    const Pack<T> cen = ldg16(x + row * CW + sub * W);
+    const T* pp = a.pp ? static_cast<const T*>(a.pp) + ch * a.chunk_stride : nullptr;
+    Pack<T> prev;
+    if (pp) prev = ldg16(pp + row * CW + sub * W);
+    Pack<T> res;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int c = c0 + w;
+        T center = cen.v[w];
+        T mr = 1;
+        if (JAC) { mr = __ldg(jr[w] + row); center *= mr; }
+        T r = acc[w] - (T)a.sigma[c] * center;
+        if (JAC) r *= mr;
+        r *= (T)a.insc[c];
+        if (pp) r -= (T)a.ppc[c] * prev.v[w];
+        res.v[w] = r;
     }
-    static_cast<T*>(a.out)[ch * a.chunk_stride + row * CW + lane] = res;
+    typename Vec16<T>::type o;
+    memcpy(&o, &res, 16);
+    *reinterpret_cast<typename Vec16<T>::type*>(static_cast<T*>(a.out) + ch * a.chunk_stride +
+                                                  row * CW + sub * W) = o;
 }
 
 }  // namespace
@@ -104,7 +156,8 @@ cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, c
     a.shift_of = r.shift_of;
     a.jac = r.jac;
     a.chunk_active = r.chunk_active;
-    const int rows_per_block = kThreads / 32;
+    constexpr int RPW = 32 / (CW / (16 / (int)sizeof(T)));
+    const int rows_per_block = (kThreads / 32) * RPW;
     dim3 grid((unsigned)((op.n + rows_per_block - 1) / rows_per_block), r.nchunk);
     if (jacobi) csr_pass_kernel<T, true><<<grid, kThreads, 0, st>>>(a);
     else csr_pass_kernel<T, false><<<grid, kThreads, 0, st>>>(a);

@@ -50,12 +50,14 @@ struct Run {
     double* quad_final;      // [ncol]  quadrature at the shift's stop step
     // per shift
     double* shifts;          // [S]
-    double* Lprev;           // [S]
+    double* Lprev;           // [S]  L_s(i-1)
+    double* Lprev2;          // [S]  L_s(i-2)
     double* Lfinal;          // [S]
     int* steps;              // [S]
     int* sdone;              // [S]
     int* chunk_active;       // [nchunk]
     int* cnt_upd;            // [nchunk]  blocks done, update kernel (last block forms beta)
+    int* nactive;            // [kmax+1]  chunks active during step i+1 (profiling)
     int* err;                // [1]
     double* part_dot;        // [nchunk][nblk][kmax][CW]  partial P_j . w
     double* part_gram;       // [nchunk][nblk][kmax][CW]  partial P_j . P_{i-1}
@@ -68,6 +70,7 @@ struct Run {
     double* tol;             // [1]
     double breakdown_rel;
     int ga;                  // 1: generalized averaged Gauss quadrature (Sec. 3.4)
+    int min_steps;           // no tolerance stop before this step
 };
 
 // Coefficients of one stencil pass (see evc_stencil.cu):
@@ -100,6 +103,7 @@ struct CsrOp {
     const int32_t* col;
     const void* val;        // T[nnz]
     const double* diag;     // double[n]
+    const int32_t* perm;    // [n] rows by decreasing length (visit order), or null
 };
 
 // Kernel launchers (T = float for EVC_MIXED, double for EVC_FP64).
@@ -121,7 +125,7 @@ cudaError_t launch_update(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_coef(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st);
-cudaError_t launch_active(const Run& r, cudaStream_t st);
+cudaError_t launch_active(const Run& r, int i, cudaStream_t st);
 
 // Host-side helpers.
 int cheb_coefficients(int degree, double a, double b, double* coef);

@@ -81,9 +81,11 @@ __global__ void init_state_kernel(Run r)
     if (t < r.S) {
         r.sdone[t] = 0;
         r.Lprev[t] = 0.0;
+        r.Lprev2[t] = 0.0;
         r.Lfinal[t] = 0.0;
         r.steps[t] = 0;
     }
+    if (t <= r.kmax) r.nactive[t] = r.nchunk;
     if (t < r.nchunk) {
         r.chunk_active[t] = 1;
         r.cnt_upd[t] = 0;
@@ -575,8 +577,13 @@ shift_kernel(Run r, int i, int last)
     if (threadIdx.x == 0) {
         const double L = red[0] / r.m;
         const double tol = *r.tol;
+        // stop rule: two consecutive changes of L_s within tol, not before
+        // step max(3, min_steps)
         int st = last ? 1 : 0;
-        if (tol > 0.0 && i >= 2 && fabs(L - r.Lprev[s]) <= tol) st = 1;
+        if (tol > 0.0 && i >= 3 && i >= r.min_steps && fabs(L - r.Lprev[s]) <= tol &&
+            fabs(r.Lprev[s] - r.Lprev2[s]) <= tol)
+            st = 1;
+        r.Lprev2[s] = r.Lprev[s];
         r.Lprev[s] = L;
         if (st) {
             r.sdone[s] = 1;
@@ -595,24 +602,35 @@ shift_kernel(Run r, int i, int last)
         }
 }
 
-// A chunk stays active while one of its real columns belongs to a running shift.
-__global__ void active_kernel(Run r)
+// A chunk stays active while one of its real columns belongs to a running
+// shift; the number of active chunks of the next step is recorded.
+__global__ void __launch_bounds__(kThreads) active_kernel(Run r, int i)
 {
-    const int ch = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ch >= r.nchunk) return;
-    int act = 0;
-    for (int l = 0; l < CW; ++l) {
-        const int c = ch * CW + l;
-        if (c < r.ncol_real && !r.sdone[r.shift_of[c]]) act = 1;
+    __shared__ int cnt[kThreads];
+    int mine = 0;
+    for (int ch = threadIdx.x; ch < r.nchunk; ch += blockDim.x) {
+        int act = 0;
+        for (int l = 0; l < CW; ++l) {
+            const int c = ch * CW + l;
+            if (c < r.ncol_real && !r.sdone[r.shift_of[c]]) act = 1;
+        }
+        r.chunk_active[ch] = act;
+        mine += act;
     }
-    r.chunk_active[ch] = act;
+    cnt[threadIdx.x] = mine;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) cnt[threadIdx.x] += cnt[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && i < r.kmax) r.nactive[i] = cnt[0];
 }
 
 }  // namespace
 
 cudaError_t launch_init_state(const Run& r, cudaStream_t st)
 {
-    const int nstate = max(max(r.ncol, r.S), r.nchunk);
+    const int nstate = max(max(max(r.ncol, r.S), r.nchunk), r.kmax + 1);
     init_state_kernel<<<(nstate + 255) / 256, 256, 0, st>>>(r);
     return cudaGetLastError();
 }
@@ -710,9 +728,9 @@ cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_active(const Run& r, cudaStream_t st)
+cudaError_t launch_active(const Run& r, int i, cudaStream_t st)
 {
-    active_kernel<<<(r.nchunk + 127) / 128, 128, 0, st>>>(r);
+    active_kernel<<<1, kThreads, 0, st>>>(r, i);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ class Workload:
     csr_builder: object = None
     nwells: int = 32
     seed: int = 0
+    min_steps: int = 3            # no tolerance stop before this step
     notes: dict = field(default_factory=dict)
 
     @property
@@ -78,25 +79,37 @@ def laplace32() -> Workload:
                     csr_builder=lambda: I.laplace2d_dirichlet(32), notes={"n": 1024})
 
 
-def batched_slicing_96(lmin: float) -> Workload:
-    """4th-order 13-point periodic 96^3 (n = 884,736), 32 shifts
-    lambda_min + 8 s/32, 64 probes, tol 0.25, at most 30 steps, Chebyshev-8."""
-    return Workload(name="slicing_96^3_13pt_cheb8_S32_m64", kind="stencil",
+# Lowest eigenvalue of the 13-point (4th-order) periodic 96^3 Hamiltonian,
+# h = 0.3, 32 wells (seed 1), by scipy.sparse.linalg.eigsh (which='SA', tol 1e-10).
+FD96_LAMBDA_MIN = -2.767709970053203
+
+
+def batched_slicing_96() -> Workload:
+    """Spectrum slicing of the 4th-order 13-point periodic 96^3 Hamiltonian
+    (n = 884,736, h = 0.3, 32 wells): 32 shifts lambda_min + 8 s/32,
+    s = 1..32, 64 probes each in one batched launch, per-shift stop at
+    tol 0.25, at least 10 and at most 30 steps, shared Chebyshev-8 kinetic
+    preconditioner."""
+    lmin = FD96_LAMBDA_MIN
+    return Workload(name="slicing_96^3_13pt_cheb8_S32_m64_tol0.25", kind="stencil",
                     shifts=[lmin + 8.0 * s / 32 for s in range(1, 33)], nprobe=64, maxsteps=30,
-                    tol=0.25, precond="cheb", prec_params=(8, 1.0), N=96, h=0.3, order=4)
+                    tol=0.25, precond="cheb", prec_params=(8, 1.0), N=96, h=0.3, order=4,
+                    min_steps=10)
 
 
 def powerlaw_2m() -> Workload:
-    """Generic sparse symmetric n = 2,000,000, power-law rows (mean ~30),
-    [-0.5, 0.5], Jacobi, 128 probes, 50 steps."""
+    """Generic sparse symmetric n = 2,000,000, power-law rows (mean ~30, at
+    most ~2000), N(0,1) values, diagonal U(-5,5), [-0.5, 0.5], Jacobi
+    1/(|d - sigma| + 1e-3), 128 probes, 50 steps."""
     return Workload(name="powerlaw_2M_jacobi_m128_k50", kind="csr", shifts=[-0.5, 0.5],
                     nprobe=128, maxsteps=50, precond="jacobi", prec_params=(1e-3, 0.0),
-                    csr_builder=lambda: I.powerlaw_symmetric(2_000_000, seed=2),
+                    csr_builder=lambda: I.powerlaw_symmetric(2_000_000, cap=2000, seed=2),
                     notes={"n": 2_000_000})
 
 
 WORKLOADS = {
     "fd64": fd_hamiltonian_64,
     "laplace32": laplace32,
+    "slicing96": batched_slicing_96,
     "powerlaw2m": powerlaw_2m,
 }

@@ -345,17 +345,20 @@ def test_count_stop_rule_and_means():
     np.testing.assert_allclose(L, quad.mean(axis=1), rtol=1e-15)
     for s, tau in enumerate(shifts):
         ks = steps[s]
-        assert 2 <= ks <= 20
+        assert 3 <= ks <= 20
         # the fixed-k run with k = ks reproduces the stopped run
-        q2, st2, L2 = O.count(P, [tau], 6, int(ks), tol=0.0, seed=4)
+        q2, _, _ = O.count(P, [tau], 6, int(ks), tol=0.0, seed=4)
         np.testing.assert_allclose(q2[0], quad[s], rtol=0, atol=1e-9)
-        # ... and the stop condition held at ks and failed before it
-        Lprev = O.count(P, [tau], 6, int(ks) - 1, seed=4)[2][0]
-        assert abs(L2[0] - Lprev) <= 0.3
-        for i in range(2, ks):
-            a = O.count(P, [tau], 6, i, seed=4)[2][0]
-            b = O.count(P, [tau], 6, i - 1, seed=4)[2][0]
-            assert abs(a - b) > 0.3
+        # the rule: two consecutive changes within tol at ks, and not at any earlier step >= 3
+        Ls = [O.count(P, [tau], 6, i, seed=4)[2][0] for i in range(1, int(ks) + 1)]
+        small = [abs(Ls[i] - Ls[i - 1]) <= 0.3 for i in range(1, len(Ls))]   # small[i-1]: step i+1
+        if ks < 20:                            # stopped by the rule, not by the cap
+            assert small[ks - 2] and small[ks - 3]
+        for i in range(3, ks):
+            assert not (small[i - 2] and small[i - 3])
+    # a minimum step count delays the stop
+    _, steps5, _ = O.count(P, shifts, 6, 20, tol=0.3, seed=4, min_steps=8)
+    assert all(s >= 8 for s in steps5)
 
 
 def test_count_columns_independent_of_batch():
