@@ -301,6 +301,107 @@ def cpu_baseline(W, nprobe_sample, seed=0):
             "seconds": round(dt, 2)}
 
 
+def run_serving(args):
+    """Serving workload: count requests on 8 resident FD Hamiltonians arriving
+    as a Poisson stream, served by the library's request server."""
+    import torch
+    from paper_1602_02306_gb300 import evc, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    evc.load()
+    Ns = [32, 40, 48, 64, 80, 96, 112, 128]
+    h = 0.3
+    ctxs, vmin = [], []
+    for N in Ns:
+        V = inputs.gaussian_wells(N, h, nwells=32, seed=1)
+        c = evc.Context.stencil(N, h, 2, V, precision=evc.EVC_MIXED)
+        c.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        # no tolerance stop before step 10: the first Ritz values have not yet
+        # reached the low end of the spectrum, where L stagnates near zero
+        evc.evc_set_option(c.h, evc.EVC_OPT_MIN_STEPS, 10)
+        ctxs.append(c)
+        vmin.append(float(V.min()))
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.85 * free)
+    srv = evc.evc_server_create(budget, slots=args.slots, max_batch=16)
+    mids = [evc.evc_server_add_matrix(srv, c.h) for c in ctxs]
+    rng = np.random.default_rng(3 + rank)
+    nreq, rate = args.requests, args.rate
+    gaps = rng.exponential(1.0 / rate, size=nreq)
+    arrive = np.cumsum(gaps)
+    reqs = []
+    for q in range(nreq):
+        mi = int(rng.integers(0, len(Ns)))
+        a, b = np.sort(rng.uniform(0.0, 4.0, size=2))
+        if b - a < 0.05:
+            b = a + 0.05
+        reqs.append(dict(matrix_id=mids[mi], xi=vmin[mi] + float(a), eta=vmin[mi] + float(b),
+                         nprobe=int(rng.choice([32, 64, 128])), maxsteps=30,
+                         tol=float(rng.choice([0.25, 0.5])), seed=3))
+    # warm-up: one request per matrix size, not timed
+    for mi in mids:
+        tk = evc.evc_server_submit(srv, mi, vmin[mi], vmin[mi] + 1.0, 32, 5, 0.0, 3)
+        evc.evc_server_wait(srv, tk)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    tickets = [None] * nreq
+    t0 = time.perf_counter()
+
+    def submitter():
+        for q in range(nreq):
+            dt = arrive[q] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[q] = evc.evc_server_submit(srv, **reqs[q])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    results = []
+    for q in range(nreq):
+        rc, r = evc.evc_server_wait(srv, tickets[q])
+        results.append((rc, r))
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = evc.evc_server_stats(srv)
+    evc.evc_server_destroy(srv)
+    for c in ctxs:
+        c.close()
+    ok = [r for rc, r in results if rc == evc.EVC_OK]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in ok])
+    first = min(r["t_submit"] for r in ok)
+    last = max(r["t_done"] for r in ok)
+    span = last - first
+    psteps = sum(q["nprobe"] * sum(r["steps"]) for q, (rc, r) in zip(reqs, results) if rc == 0)
+    value = psteps / span
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": nreq, "warmup": len(mids), "ms_per_step": round(1000 * span / max(1, len(ok)), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serving_8x_fd_7pt_32^3-128^3_jacobi", "requests": nreq,
+                       "offered_rps": rate, "slots": args.slots, "max_batch": 16,
+                       "hbm_budget_GB": round(budget / 1e9, 1),
+                       "probes": [32, 64, 128], "tol": [0.25, 0.5], "maxsteps": 30,
+                       "min_steps": 10,
+                       "step": "one request (2 shifts x m probes, early stop)"},
+            "serving": {"completed": len(ok), "failed": nreq - len(ok),
+                        "throughput_rps": round(len(ok) / span, 2),
+                        "p50_ms": round(1000 * float(np.percentile(lat, 50)), 2),
+                        "p99_ms": round(1000 * float(np.percentile(lat, 99)), 2),
+                        "mean_batch": round(float(np.mean([r["batch_size"] for r in ok])), 2),
+                        "merged": st["merged"], "batches": st["batches"],
+                        "peak_hbm_GB": round(st["peak_bytes"] / 1e9, 2), "wall_s": round(wall, 2),
+                        "mean_steps": round(float(np.mean([np.mean(r["steps"]) for r in ok])), 2)},
+            "clocks": clk,
+            "e2e": {"value": round(value, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * 3,
+                    "path": "evc_server_submit/wait (host arguments and results)"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -341,9 +442,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison leg")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg")
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per s")
+    ap.add_argument("--slots", type=int, default=4, help="serving workload: server slots")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -44,7 +44,8 @@ typedef enum {
     EVC_ECUDA = 3,         /* a CUDA runtime call failed                         */
     EVC_ENUMERIC = 4,      /* NaN/Inf in alpha/beta or eigensolver did not converge */
     EVC_ETIMEOUT = 5,      /* a bounded device wait gave up                      */
-    EVC_EUNSUPPORTED = 6   /* valid request this build does not implement        */
+    EVC_EUNSUPPORTED = 6,  /* valid request this build does not implement        */
+    EVC_EAGAIN = 7         /* a server request has not finished yet              */
 } evc_status;
 
 /* Arithmetic of the path.
@@ -224,6 +225,72 @@ typedef struct {
  * (may be NULL) and the number of kernel launches of one call to *nrec.
  * Synchronises the context's stream.                                          */
 int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
+
+/* ------------------------------------------------------------------------
+ * Request server: interval counts on several resident matrices, served as
+ * requests arrive (the spectrum-slicing use of Sec. 1, many independent
+ * counts).
+ *
+ * A scheduler thread keeps the waiting requests in arrival order.  Whenever
+ * one of `slots` execution slots is idle it forms a batch: the oldest waiting
+ * request plus later requests that can share its launch (same matrix,
+ * nprobe, maxsteps, tol and seed), at most max_batch of them and only as many
+ * as fit the HBM budget (the batch's workspace, evc_workspace_bytes of
+ * 2 shifts per request).  A batch is one evc_count_slices on the slot's own
+ * stream, so batches on different slots overlap on the device; memory and
+ * slots return when a batch ends and waiting requests are admitted then.
+ * The oldest request is never overtaken; one that cannot fit even with
+ * nothing running fails with EVC_ENOMEM.  Each request's result equals the
+ * result of the same request run alone (columns are independent and every
+ * reduction has a batch-independent order).
+ * ------------------------------------------------------------------------ */
+typedef struct evc_server evc_server;
+
+typedef struct {
+    int32_t status;       /* evc_status of the request                          */
+    int32_t batch_size;   /* requests that shared its launch                    */
+    double estimate;      /* L_eta - L_xi                                        */
+    double n_below[2];    /* L_xi, L_eta                                         */
+    int32_t steps[2];     /* Lanczos steps used per shift                        */
+    double t_submit;      /* seconds since the server started: submission,      */
+    double t_start;       /*   admission of its batch,                          */
+    double t_done;        /*   completion                                       */
+} evc_result;
+
+typedef struct {
+    uint64_t budget_bytes, used_bytes, peak_bytes;   /* HBM admission accounting */
+    int64_t pending;      /* requests waiting                                   */
+    int64_t batches;      /* batches launched                                   */
+    int64_t completed;    /* requests finished                                  */
+    int64_t merged;       /* requests that joined another request's batch       */
+} evc_server_counters;
+
+/* hbm_budget_bytes: device memory the workspaces of running batches may use
+ * together; slots: batches in flight at once (1..64); max_batch: requests
+ * per batch (1..1024).  Uses the current CUDA device.                         */
+int evc_server_create(size_t hbm_budget_bytes, int slots, int max_batch, evc_server** out);
+
+/* Register a configured context (matrix + preconditioner + options); the
+ * server borrows it (it must outlive the server).  *matrix_id receives its id. */
+int evc_server_add_matrix(evc_server* srv, evc_ctx* ctx, int* matrix_id);
+
+/* Queue one count of the eigenvalues in [xi, eta] (arguments as evc_count).
+ * per_probe_quad: optional host buffer of 2*nprobe doubles, filled on
+ * completion; it must stay valid until then.  Returns at once.                */
+int evc_server_submit(evc_server* srv, int matrix_id, double xi, double eta, int nprobe,
+                      int maxsteps, double tol, uint64_t seed, double* per_probe_quad,
+                      int64_t* ticket);
+
+/* Result of a finished request: EVC_EAGAIN while it is still queued or
+ * running; otherwise the request's status, *res filled and the ticket
+ * released.  evc_server_wait blocks up to timeout_s seconds (< 0: forever).  */
+int evc_server_poll(evc_server* srv, int64_t ticket, evc_result* res);
+int evc_server_wait(evc_server* srv, int64_t ticket, double timeout_s, evc_result* res);
+
+int evc_server_stats(evc_server* srv, evc_server_counters* stats);
+
+/* Finish every queued request, then stop the threads and free the server.     */
+void evc_server_destroy(evc_server* srv);
 
 /* Allocation-free batched Gauss quadrature.  The paper has no counterpart.
  *

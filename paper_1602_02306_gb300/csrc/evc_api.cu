@@ -120,13 +120,15 @@ int fail(evc_ctx* c, int code, const char* fmt, ...)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int choose_nblk(int64_t n, int nchunk)
+// Row blocks per chunk of the reorthogonalisation kernels.  It depends on n
+// only, never on how many chunks share the launch, so the summation order of
+// every dot product -- and therefore every result -- is the same whether a
+// column runs alone or batched with others.  3456 rows per block (54 tiles
+// of the update kernel) keeps each block's bulk-copy pipeline long; the
+// 64^3 Hamiltonian with four chunks gets 304 blocks, two per SM.
+int choose_nblk(int64_t n)
 {
-    // two resident blocks per SM of the streaming reorthogonalisation kernels
-    // on 152 SMs; at least 64 rows per block
-    const int64_t target = (2 * 152 + nchunk - 1) / nchunk;
-    const int64_t maxb = std::max<int64_t>(1, (n + 63) / 64);
-    return (int)std::max<int64_t>(1, std::min(target, maxb));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 3455) / 3456, 65535));
 }
 
 struct Layout {
@@ -145,7 +147,7 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     const int ncol_real = S * m;
     const int nchunk = (ncol_real + CW - 1) / CW;
     const int ncol = nchunk * CW;
-    const int nblk = choose_nblk(c->n, nchunk);
+    const int nblk = choose_nblk(c->n);
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -754,6 +756,42 @@ evc_ctx* new_ctx(int precision, void* stream)
 }
 
 }  // namespace
+
+// A context that computes on the same matrix and preconditioner as src, on a
+// stream of its own (non-blocking), without a workspace; the matrix arrays
+// are borrowed from src, which must outlive it.  Used by the request server
+// so that several launches on one matrix can be in flight at once.
+evc_ctx* evc::clone_context(const evc_ctx* src)
+{
+    evc_ctx* c = new (std::nothrow) evc_ctx();
+    if (!c) return nullptr;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return nullptr;
+    }
+    c->own_stream = true;
+    c->op = src->op;
+    c->precision = src->precision;
+    c->tsize = src->tsize;
+    c->n = src->n;
+    c->csr = src->csr;
+    c->nnz = src->nnz;
+    c->sten = src->sten;
+    c->prec = src->prec;
+    c->jac_eps = src->jac_eps;
+    c->cheb_degree = src->cheb_degree;
+    c->cheb_c = src->cheb_c;
+    c->cheb_a = src->cheb_a;
+    c->cheb_b = src->cheb_b;
+    c->cheb_coef = src->cheb_coef;
+    c->quad_rule = src->quad_rule;
+    c->min_steps = src->min_steps;
+    c->use_graph = false;
+    return c;
+}
+
+cudaStream_t evc::ctx_stream(const evc_ctx* c) { return c->stream; }
 
 // ================================================================== C ABI
 

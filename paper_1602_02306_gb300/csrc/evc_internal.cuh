@@ -131,3 +131,10 @@ cudaError_t launch_active(const Run& r, int i, cudaStream_t st);
 int cheb_coefficients(int degree, double a, double b, double* coef);
 
 }  // namespace evc
+
+struct evc_ctx;
+namespace evc {
+evc_ctx* clone_context(const evc_ctx* src);
+cudaStream_t ctx_stream(const evc_ctx* c);
+
+}  // namespace evc

@@ -22,7 +22,8 @@ _LIB_PATH = os.path.join(_PKG, "libevc.so")
 _lock = threading.Lock()
 _lib = None
 
-EVC_OK, EVC_EINVAL, EVC_ENOMEM, EVC_ECUDA, EVC_ENUMERIC, EVC_ETIMEOUT, EVC_EUNSUPPORTED = range(7)
+(EVC_OK, EVC_EINVAL, EVC_ENOMEM, EVC_ECUDA, EVC_ENUMERIC, EVC_ETIMEOUT, EVC_EUNSUPPORTED,
+ EVC_EAGAIN) = range(8)
 EVC_FP64, EVC_MIXED = 0, 1
 EVC_PREC_IDENTITY, EVC_PREC_JACOBI, EVC_PREC_CHEB_KINETIC = 0, 1, 2
 EVC_OPT_GRAPH, EVC_OPT_PROFILE, EVC_OPT_QUADRATURE, EVC_OPT_MIN_STEPS = 1, 2, 3, 4
@@ -37,8 +38,9 @@ EXPORTED = [
     "evc_create_csr", "evc_create_stencil", "evc_set_values", "evc_set_precond",
     "evc_workspace_bytes", "evc_set_workspace", "evc_count", "evc_count_slices",
     "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_set_option",
-    "evc_get_profile", "evc_gauss_quadrature_static", "evc_last_error", "evc_destroy",
-    "evc_version",
+    "evc_get_profile", "evc_server_create", "evc_server_add_matrix", "evc_server_submit",
+    "evc_server_poll", "evc_server_wait", "evc_server_stats", "evc_server_destroy",
+    "evc_gauss_quadrature_static", "evc_last_error", "evc_destroy", "evc_version",
 ]
 
 
@@ -56,6 +58,18 @@ class evc_csr(C.Structure):
 
 class evc_prof_rec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("step", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+class evc_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("batch_size", C.c_int32), ("estimate", C.c_double),
+                ("n_below", C.c_double * 2), ("steps", C.c_int32 * 2), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class evc_server_counters(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("used_bytes", C.c_uint64),
+                ("peak_bytes", C.c_uint64), ("pending", C.c_int64), ("batches", C.c_int64),
+                ("completed", C.c_int64), ("merged", C.c_int64)]
 
 
 def lib_path() -> str:
@@ -90,6 +104,14 @@ def load(path: str | None = None):
             "evc_get_tridiag": (i32, [vp, dp, dp, ip]),
             "evc_set_option": (i32, [vp, i32, i64]),
             "evc_get_profile": (i32, [vp, C.POINTER(evc_prof_rec), i32, ip]),
+            "evc_server_create": (i32, [C.c_size_t, i32, i32, pp]),
+            "evc_server_add_matrix": (i32, [vp, vp, ip]),
+            "evc_server_submit": (i32, [vp, i32, d, d, i32, i32, d, u64, vp,
+                                        C.POINTER(C.c_int64)]),
+            "evc_server_poll": (i32, [vp, C.c_int64, C.POINTER(evc_result)]),
+            "evc_server_wait": (i32, [vp, C.c_int64, d, C.POINTER(evc_result)]),
+            "evc_server_stats": (i32, [vp, C.POINTER(evc_server_counters)]),
+            "evc_server_destroy": (None, [vp]),
             "evc_gauss_quadrature_static": (i32, [vp, vp, vp, i32, i32, d, vp, vp, C.c_char_p,
                                                   C.c_size_t]),
             "evc_last_error": (C.c_char_p, [vp]),
@@ -229,6 +251,66 @@ def evc_get_profile(ctx):
 
 
 EVC_STATIC_QUAD_MAX = 262144
+
+
+# ------------------------------------------------------------------ server
+
+def _result_dict(r):
+    return {"status": r.status, "batch_size": r.batch_size, "estimate": r.estimate,
+            "n_below": [r.n_below[0], r.n_below[1]], "steps": [r.steps[0], r.steps[1]],
+            "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done}
+
+
+def evc_server_create(budget_bytes, slots=4, max_batch=16):
+    out = C.c_void_p()
+    rc = load().evc_server_create(int(budget_bytes), slots, max_batch, C.byref(out))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_server_create failed")
+    return out.value
+
+
+def evc_server_add_matrix(srv, ctx):
+    mid = C.c_int(0)
+    rc = load().evc_server_add_matrix(srv, ctx, C.byref(mid))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_server_add_matrix failed")
+    return mid.value
+
+
+def evc_server_submit(srv, matrix_id, xi, eta, nprobe, maxsteps, tol=0.0, seed=0, quad_buf=None):
+    """quad_buf: optional float64 numpy array of 2*nprobe, filled on completion."""
+    t = C.c_int64(0)
+    ptr = quad_buf.ctypes.data if quad_buf is not None else None
+    rc = load().evc_server_submit(srv, matrix_id, xi, eta, nprobe, maxsteps, tol, C.c_uint64(seed),
+                                  ptr, C.byref(t))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_server_submit failed")
+    return t.value
+
+
+def evc_server_wait(srv, ticket, timeout_s=-1.0):
+    r = evc_result()
+    rc = load().evc_server_wait(srv, ticket, timeout_s, C.byref(r))
+    return rc, _result_dict(r)
+
+
+def evc_server_poll(srv, ticket):
+    r = evc_result()
+    rc = load().evc_server_poll(srv, ticket, C.byref(r))
+    return rc, _result_dict(r)
+
+
+def evc_server_stats(srv):
+    st = evc_server_counters()
+    rc = load().evc_server_stats(srv, C.byref(st))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_server_stats failed")
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def evc_server_destroy(srv):
+    if srv:
+        load().evc_server_destroy(srv)
 
 
 def evc_gauss_quadrature_static(d_alpha, d_beta, d_kcol, k, ncol, vnorm2, d_quad, stream=None):
