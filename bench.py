@@ -135,7 +135,25 @@ def _roofline(evc, recs, peak, peak_kind):
             "launches": cnt, "share_of_step": None}
     tot = sum(v["ms"] for v in per_kind.values())
     roof["share_of_step"] = round(t / tot, 3) if tot > 0 else None
+    _attach_traffic(roof)
     return roof, per_kind
+
+
+def _attach_traffic(roof):
+    """DRAM traffic of one launch of the dominant kernel from the committed ncu
+    capture, only while the kernel's source is unchanged since the capture."""
+    import hashlib
+    rec = {"stencil_pass_kernel": "profiles/stencil_pass_fd64_traffic.json"}.get(roof["kernel"])
+    if not rec or not os.path.exists(os.path.join(ROOT, rec)):
+        return
+    d = json.load(open(os.path.join(ROOT, rec)))
+    src = os.path.join(ROOT, d["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d["source_sha256"]:
+        return
+    roof["traffic"] = d["dram_bytes"]
+    roof["traffic_launch"] = d["launch"]
+    roof["traffic_launch_algorithmic_bytes"] = d["algorithmic_bytes"]
+    roof["traffic_source"] = d["profile"]
 
 
 def run_ours(args):
