@@ -193,8 +193,18 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       Eq. GA_Tk).  Same Lanczos steps, different step 5 of
  *                       Algorithm 2.
  *   EVC_OPT_MIN_STEPS : under a tolerance (tol > 0), no shift stops before
- *                       this step (default 3, at least 3).                   */
-enum { EVC_OPT_GRAPH = 1, EVC_OPT_PROFILE = 2, EVC_OPT_QUADRATURE = 3, EVC_OPT_MIN_STEPS = 4 };
+ *                       this step (default 3, at least 3).
+ *   EVC_OPT_PROBE_OFFSET: the calls that follow use probe ids offset..offset+
+ *                       nprobe-1 (default 0), so that shards of one count can
+ *                       run on different GPUs and be combined: the union of the
+ *                       shards is the same probe set as one unsharded call.  */
+enum {
+    EVC_OPT_GRAPH = 1,
+    EVC_OPT_PROFILE = 2,
+    EVC_OPT_QUADRATURE = 3,
+    EVC_OPT_MIN_STEPS = 4,
+    EVC_OPT_PROBE_OFFSET = 5
+};
 enum { EVC_QUAD_GAUSS = 0, EVC_QUAD_GA = 1 };
 int evc_set_option(evc_ctx* ctx, int option, int64_t value);
 

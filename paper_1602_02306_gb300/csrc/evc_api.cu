@@ -70,6 +70,7 @@ struct evc_ctx {
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
     int min_steps = 3;
+    int64_t probe_offset = 0;
     // workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -615,7 +616,8 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
         const int s = real ? c / m : S - 1;
         hsh[c] = s;
         hsig[c] = shifts[s];
-        hpid[c] = real ? c % m : (int64_t)m + (c - S * m);   // padding: extra probes, ignored
+        // probe ids probe_offset + j; padding columns run extra probes, ignored
+        hpid[c] = ctx->probe_offset + (real ? c % m : (int64_t)m + (c - S * m));
     }
     for (int s = 0; s < S; ++s) hshifts[s] = shifts[s];
     *hseed = seed;
@@ -787,6 +789,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->cheb_coef = src->cheb_coef;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
+    c->probe_offset = src->probe_offset;
     c->use_graph = false;
     return c;
 }
@@ -1127,6 +1130,12 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         ctx->min_steps = (int)value;
         ++ctx->prec_version;
         drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_PROBE_OFFSET) {
+        if (value < 0 || value > ((int64_t)1 << 31))
+            return fail(ctx, EVC_EINVAL, "probe offset must be in [0, 2^31]");
+        ctx->probe_offset = value;     // a per-call upload, no graph change
         return EVC_OK;
     }
     if (option == EVC_OPT_QUADRATURE) {

@@ -26,7 +26,7 @@ _lib = None
  EVC_EAGAIN) = range(8)
 EVC_FP64, EVC_MIXED = 0, 1
 EVC_PREC_IDENTITY, EVC_PREC_JACOBI, EVC_PREC_CHEB_KINETIC = 0, 1, 2
-EVC_OPT_GRAPH, EVC_OPT_PROFILE, EVC_OPT_QUADRATURE, EVC_OPT_MIN_STEPS = 1, 2, 3, 4
+EVC_OPT_GRAPH, EVC_OPT_PROFILE, EVC_OPT_QUADRATURE, EVC_OPT_MIN_STEPS, EVC_OPT_PROBE_OFFSET = 1, 2, 3, 4, 5
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1
 (EVC_K_INIT, EVC_K_JACOBI, EVC_K_STENCIL, EVC_K_CSR, EVC_K_DOTS, EVC_K_REDUCE, EVC_K_UPDATE,
  EVC_K_FINISH) = range(8)

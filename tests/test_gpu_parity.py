@@ -314,3 +314,17 @@ def test_ga_adaptive_csr_fp64():
     qr, sr, Lr = O.count(P, shifts, 12, 40, tol=0.25, seed=0, rule=1)
     assert list(st) == list(sr)
     assert np.max(np.abs(q - qr)) < FP64_TOL
+
+
+def test_probe_offset_shards_concatenate_to_the_unsharded_count():
+    # sharding one count by probes (one GPU per shard) gives the same columns
+    N, h = 12, 0.3
+    V = I.gaussian_wells(N, h, nwells=6, seed=1)
+    with evc.Context.stencil(N, h, 2, V, precision=evc.EVC_MIXED) as ctx:
+        ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, 8, 1.0)
+        L, q, _ = ctx.count_slices([-2.0, 0.5], 40, 12, seed=5)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_PROBE_OFFSET, 0)
+        _, qa, _ = ctx.count_slices([-2.0, 0.5], 25, 12, seed=5)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_PROBE_OFFSET, 25)
+        _, qb, _ = ctx.count_slices([-2.0, 0.5], 15, 12, seed=5)
+    np.testing.assert_array_equal(np.concatenate([qa, qb], axis=1), q)
