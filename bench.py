@@ -93,6 +93,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_CHEB_FORM = [0]     # EVC_CHEB_FACTORED; --cheb-form clenshaw sets 1
+
+
 def _make_ctx(evc, W, precision, stream_ptr, V=None):
     if W.kind == "stencil":
         ctx = evc.Context.stencil(W.N, W.h, W.order, W.potential() if V is None else V,
@@ -103,6 +106,8 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
             "cheb": evc.EVC_PREC_CHEB_KINETIC}[W.precond]
     ctx.set_precond(kind, *W.prec_params)
     evc.evc_set_option(ctx.h, evc.EVC_OPT_MIN_STEPS, W.min_steps)
+    if W.precond == "cheb":
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_CHEB_FORM, _CHEB_FORM[0])
     ctx.reserve(len(W.shifts), W.nprobe, W.maxsteps)
     return ctx
 
@@ -271,7 +276,8 @@ def run_ours(args):
         "config": {"workload": W.name, "n": W.n, "shifts": S, "probes_per_shift": m,
                    "lanczos_steps_max": k, "tol": W.tol,
                    "steps_used": [int(x) for x in steps_mixed],
-                   "precond": {"cheb": f"chebyshev-{int(W.prec_params[0])} kinetic (c={W.prec_params[1]})",
+                   "precond": {"cheb": f"chebyshev-{int(W.prec_params[0])} kinetic (c={W.prec_params[1]}), "
+                                       f"{['factored', 'clenshaw'][_CHEB_FORM[0]]}",
                                "jacobi": "jacobi (eps 1e-3)", "identity": "none"}[W.precond],
                    "precision": "FP32 vectors/operator, FP64 alpha/beta/reorth coefficients/eig",
                    "step": "one full count: all shifts x probes x executed Lanczos steps",
@@ -467,7 +473,10 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per s")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: server slots")
+    ap.add_argument("--cheb-form", default="factored", choices=["factored", "clenshaw"],
+                    help="how the Chebyshev preconditioner polynomial is applied")
     args = ap.parse_args()
+    _CHEB_FORM[0] = 0 if args.cheb_form == "factored" else 1
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":

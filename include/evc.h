@@ -197,14 +197,25 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *   EVC_OPT_PROBE_OFFSET: the calls that follow use probe ids offset..offset+
  *                       nprobe-1 (default 0), so that shards of one count can
  *                       run on different GPUs and be combined: the union of the
- *                       shards is the same probe set as one unsharded call.  */
+ *                       shards is the same probe set as one unsharded call.
+ *   EVC_OPT_CHEB_FORM : how M = p_d(K) is applied.  EVC_CHEB_FACTORED (default)
+ *                       multiplies the factors of p_d (roots found when the
+ *                       preconditioner is set; a conjugate pair of roots gives
+ *                       the factor (K - re)^2 + im^2, two passes that move 5
+ *                       vectors); EVC_CHEB_CLENSHAW runs Clenshaw's recurrence,
+ *                       one pass per degree moving 4 vectors.  The same operator
+ *                       up to rounding.  When the factorisation fails its check
+ *                       at EVC_PREC_CHEB_KINETIC time, Clenshaw's recurrence is
+ *                       used whatever this option says.  */
 enum {
     EVC_OPT_GRAPH = 1,
     EVC_OPT_PROFILE = 2,
     EVC_OPT_QUADRATURE = 3,
     EVC_OPT_MIN_STEPS = 4,
-    EVC_OPT_PROBE_OFFSET = 5
+    EVC_OPT_PROBE_OFFSET = 5,
+    EVC_OPT_CHEB_FORM = 6
 };
+enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };
 enum { EVC_QUAD_GAUSS = 0, EVC_QUAD_GA = 1 };
 int evc_set_option(evc_ctx* ctx, int option, int64_t value);
 

@@ -15,6 +15,7 @@
 #include "../../include/evc.h"
 
 #include <algorithm>
+#include <complex>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -67,6 +68,12 @@ struct evc_ctx {
     double cheb_c = 1.0;
     double cheb_a = 0, cheb_b = 0;
     std::vector<double> cheb_coef;
+    // p_d in factored form (roots of p_d): conjugate pairs (re +- i im) and
+    // real roots, empty when the factorisation failed its check
+    struct ChebFactor { double re, im; bool pair; };
+    std::vector<ChebFactor> cheb_fac;
+    double cheb_g = 1.0, cheb_sign = 1.0;   // |leading coefficient|^(1/d), its sign
+    int cheb_form = EVC_CHEB_FACTORED;
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
     int min_steps = 3;
@@ -297,6 +304,107 @@ double cheb_eval(const std::vector<double>& c, double a, double b, double x)
     return c[0] + t * b1 - b2;
 }
 
+// p(t) = sum_j c_j T_j(t) and p'(t) for complex t (Clenshaw summation; dc are
+// the Chebyshev coefficients of p').
+void cheb_val_der(const std::vector<double>& c, const std::vector<double>& dc,
+                  std::complex<double> t, std::complex<double>& p, std::complex<double>& dp)
+{
+    auto clen = [&](const std::vector<double>& cc) {
+        std::complex<double> b1 = 0.0, b2 = 0.0;
+        for (int j = (int)cc.size() - 1; j >= 1; --j) {
+            const std::complex<double> b0 = cc[j] + 2.0 * t * b1 - b2;
+            b2 = b1;
+            b1 = b0;
+        }
+        return cc.empty() ? std::complex<double>(0.0) : cc[0] + t * b1 - b2;
+    };
+    p = clen(c);
+    dp = clen(dc);
+}
+
+// Roots of p_d (Aberth-Ehrlich simultaneous iteration on the Chebyshev series
+// in t = (2x - a - b)/(b - a)), mapped to x and sorted into conjugate pairs
+// (ascending real part) followed by real roots.  The factored product
+//   sign * prod_pairs g^2 ((x - re)^2 + im^2) * prod_reals g (x - r)
+// must reproduce p_d on [a, b] to 1e-9 relative, else false.
+bool cheb_factor(const std::vector<double>& c, double a, double b,
+                 std::vector<evc_ctx::ChebFactor>& fac, double& g, double& sgn)
+{
+    typedef std::complex<double> cd;
+    const int d = (int)c.size() - 1;
+    fac.clear();
+    if (d < 1 || c[d] == 0.0) return false;
+    std::vector<double> tmp(d + 2, 0.0);
+    for (int k = d; k >= 1; --k) tmp[k - 1] = tmp[k + 1] + 2.0 * k * c[k];
+    tmp[0] *= 0.5;
+    std::vector<double> dc(tmp.begin(), tmp.begin() + d);
+    std::vector<cd> z(d);
+    const double pi = 3.141592653589793238462643;
+    for (int k = 0; k < d; ++k) z[k] = std::polar(1.3, 2.0 * pi * k / d + 0.4);
+    for (int it = 0; it < 2000; ++it) {
+        double mx = 0.0;
+        for (int k = 0; k < d; ++k) {
+            cd p, dp;
+            cheb_val_der(c, dc, z[k], p, dp);
+            if (std::abs(p) == 0.0) continue;
+            const cd ratio = p / dp;
+            cd sum = 0.0;
+            for (int j = 0; j < d; ++j)
+                if (j != k) sum += 1.0 / (z[k] - z[j]);
+            const cd w = ratio / (1.0 - ratio * sum);
+            if (!std::isfinite(w.real()) || !std::isfinite(w.imag())) return false;
+            z[k] -= w;
+            mx = std::max(mx, std::abs(w) / (1.0 + std::abs(z[k])));
+        }
+        if (mx < 1e-15) break;
+    }
+    std::vector<cd> x(d);
+    for (int k = 0; k < d; ++k) x[k] = 0.5 * (b - a) * z[k] + 0.5 * (a + b);
+    std::vector<bool> used(d, false);
+    std::vector<evc_ctx::ChebFactor> pairs, reals;
+    for (int k = 0; k < d; ++k) {
+        if (used[k]) continue;
+        if (std::abs(x[k].imag()) <= 1e-9 * (1.0 + std::abs(x[k]))) {
+            used[k] = true;
+            reals.push_back({x[k].real(), 0.0, false});
+            continue;
+        }
+        int best = -1;
+        double bd = 1e300;
+        for (int j = 0; j < d; ++j) {
+            if (j == k || used[j]) continue;
+            const double dist = std::abs(x[j] - std::conj(x[k]));
+            if (dist < bd) {
+                bd = dist;
+                best = j;
+            }
+        }
+        if (best < 0 || bd > 1e-7 * (1.0 + std::abs(x[k]))) return false;
+        used[k] = used[best] = true;
+        pairs.push_back({0.5 * (x[k].real() + x[best].real()), std::abs(x[k].imag()), true});
+    }
+    auto by_re = [](const evc_ctx::ChebFactor& u, const evc_ctx::ChebFactor& v) { return u.re < v.re; };
+    std::sort(pairs.begin(), pairs.end(), by_re);
+    std::sort(reals.begin(), reals.end(), by_re);
+    fac = pairs;
+    fac.insert(fac.end(), reals.begin(), reals.end());
+    const double lead = c[d] * std::ldexp(1.0, d - 1) * std::pow(2.0 / (b - a), d);
+    g = std::pow(std::fabs(lead), 1.0 / d);
+    sgn = lead < 0 ? -1.0 : 1.0;
+    for (int m = 0; m <= 4000; ++m) {
+        const double xx = a + (b - a) * m / 4000.0;
+        double prod = sgn;
+        for (const auto& f : fac)
+            prod *= f.pair ? g * g * ((xx - f.re) * (xx - f.re) + f.im * f.im) : g * (xx - f.re);
+        const double ref = cheb_eval(c, a, b, xx);
+        if (!(std::fabs(prod - ref) <= 1e-9 * std::max(std::fabs(ref), 1e-300))) {
+            fac.clear();
+            return false;
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 int evc::cheb_coefficients(int degree, double a, double b, double* coef)
@@ -377,11 +485,85 @@ int stencil(evc_ctx* ctx, const Run& r, int step, const StencilPass& p, bool jac
 // y = c_0 x + K~ b_1 - b_2, K~ = (2K - (a+b)I)/(b-a).  Terms that are still
 // multiples of x are folded into the next pass, so degree d costs d passes;
 // b_j overwrites b_{j+2} in place (it is read only at its own point).
+// y = p_d(K) x in factored form: for each conjugate pair of roots of p_d,
+//   u = g (K - re) x,   x <- g (K - re) u + g^2 im^2 x
+// (two passes that move 5 vectors per degree 2, against 8 for two Clenshaw
+// steps), then one pass g (K - r) per real root; the sign of the leading
+// coefficient and the "- beta_i q_{i-1}" term ride on the last pass.  The
+// shifted quadratic form has no cancellation; the factorisation is checked
+// against the series when the preconditioner is set.  Wa is scratch; the
+// running product lives in Wb (updated in place: a pass reads its x operand
+// only at its own point).
+template <typename T>
+int enqueue_cheb_factored(evc_ctx* ctx, const Run& r, int step, const void* x, int64_t x_cs,
+                          const double* xscale, void* Wa, void* Wb, void* out, int64_t out_cs,
+                          const void* pp, int64_t pp_cs, const double* ppc)
+{
+    const int64_t wcs = r.n * CW;
+    const double g = ctx->cheb_g, c = ctx->cheb_c;
+    const void* cur = x;
+    int64_t cur_cs = x_cs;
+    const double* cur_sc = xscale;
+    const size_t nf = ctx->cheb_fac.size();
+    for (size_t f = 0; f < nf; ++f) {
+        const evc_ctx::ChebFactor& F = ctx->cheb_fac[f];
+        const bool last = f + 1 == nf;
+        const double sg = last ? ctx->cheb_sign : 1.0;
+        void* dst = last ? out : Wb;
+        const int64_t dst_cs = last ? out_cs : wcs;
+        StencilPass p{};
+        if (F.pair) {
+            StencilPass pa{};
+            pa.in = cur;
+            pa.in_cs = cur_cs;
+            pa.insc = cur_sc;
+            pa.k1 = g;
+            pa.k0 = g * (c - F.re);
+            pa.out = Wa;
+            pa.out_cs = wcs;
+            int rc = stencil<T>(ctx, r, step, pa, false);
+            if (rc) return rc;
+            p.in = Wa;
+            p.in_cs = wcs;
+            p.k1 = sg * g;
+            p.k0 = sg * g * (c - F.re);
+            p.x = cur;
+            p.x_cs = cur_cs;
+            p.xs = cur_sc;
+            p.a0 = sg * g * g * F.im * F.im;
+        } else {
+            // reads cur with its halo: never in place
+            if (!last && cur == Wb) dst = Wa;
+            p.in = cur;
+            p.in_cs = cur_cs;
+            p.insc = cur_sc;
+            p.k1 = sg * g;
+            p.k0 = sg * g * (c - F.re);
+        }
+        p.out = dst;
+        p.out_cs = dst_cs;
+        if (last) {
+            p.pp = pp;
+            p.pp_cs = pp_cs;
+            p.ppc = pp ? ppc : nullptr;
+        }
+        int rc = stencil<T>(ctx, r, step, p, false);
+        if (rc) return rc;
+        cur = dst;
+        cur_cs = dst_cs;
+        cur_sc = nullptr;
+    }
+    return EVC_OK;
+}
+
 template <typename T>
 int enqueue_cheb(evc_ctx* ctx, const Run& r, int step, const void* x, int64_t x_cs,
                  const double* xscale, void* W0, void* W1, void* out, int64_t out_cs,
                  const void* pp, int64_t pp_cs, const double* ppc)
 {
+    if (ctx->cheb_form == EVC_CHEB_FACTORED && !ctx->cheb_fac.empty())
+        return enqueue_cheb_factored<T>(ctx, r, step, x, x_cs, xscale, W0, W1, out, out_cs, pp,
+                                        pp_cs, ppc);
     const int d = ctx->cheb_degree;
     const std::vector<double>& c = ctx->cheb_coef;
     const double a = ctx->cheb_a, b = ctx->cheb_b;
@@ -787,6 +969,10 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->cheb_a = src->cheb_a;
     c->cheb_b = src->cheb_b;
     c->cheb_coef = src->cheb_coef;
+    c->cheb_fac = src->cheb_fac;
+    c->cheb_g = src->cheb_g;
+    c->cheb_sign = src->cheb_sign;
+    c->cheb_form = src->cheb_form;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
     c->probe_offset = src->probe_offset;
@@ -996,6 +1182,8 @@ int evc_set_precond(evc_ctx* ctx, int kind, double param0, double param1)
         ctx->cheb_a = a;
         ctx->cheb_b = b;
         ctx->cheb_coef = coef;
+        if (!cheb_factor(coef, a, b, ctx->cheb_fac, ctx->cheb_g, ctx->cheb_sign))
+            ctx->cheb_fac.clear();   // Clenshaw's recurrence only
     } else {
         return fail(ctx, EVC_EINVAL, "unknown preconditioner kind %d", kind);
     }
@@ -1136,6 +1324,14 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         if (value < 0 || value > ((int64_t)1 << 31))
             return fail(ctx, EVC_EINVAL, "probe offset must be in [0, 2^31]");
         ctx->probe_offset = value;     // a per-call upload, no graph change
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_CHEB_FORM) {
+        if (value != EVC_CHEB_FACTORED && value != EVC_CHEB_CLENSHAW)
+            return fail(ctx, EVC_EINVAL, "unknown Chebyshev evaluation form %lld", (long long)value);
+        ctx->cheb_form = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
         return EVC_OK;
     }
     if (option == EVC_OPT_QUADRATURE) {

@@ -27,6 +27,8 @@ _lib = None
 EVC_FP64, EVC_MIXED = 0, 1
 EVC_PREC_IDENTITY, EVC_PREC_JACOBI, EVC_PREC_CHEB_KINETIC = 0, 1, 2
 EVC_OPT_GRAPH, EVC_OPT_PROFILE, EVC_OPT_QUADRATURE, EVC_OPT_MIN_STEPS, EVC_OPT_PROBE_OFFSET = 1, 2, 3, 4, 5
+EVC_OPT_CHEB_FORM = 6
+EVC_CHEB_FACTORED, EVC_CHEB_CLENSHAW = 0, 1
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1
 (EVC_K_INIT, EVC_K_JACOBI, EVC_K_STENCIL, EVC_K_CSR, EVC_K_DOTS, EVC_K_REDUCE, EVC_K_UPDATE,
  EVC_K_FINISH) = range(8)
@@ -354,6 +356,10 @@ class Context:
 
     def set_precond(self, kind, p0=0.0, p1=0.0):
         evc_set_precond(self.h, kind, p0, p1)
+        return self
+
+    def set_option(self, option, value):
+        evc_set_option(self.h, option, value)
         return self
 
     def reserve(self, nshift, nprobe, maxsteps):
