@@ -212,6 +212,9 @@ def run_ours(args):
     # ---- headline: FP32-mixed, inputs resident
     ctx = _make_ctx(evc, W, evc.EVC_MIXED, sp)
     ws_mixed = evc.evc_workspace_bytes(ctx.h, S, m, k)
+    # the library's autotuner picks the tile shapes for this launch shape
+    # (short counts, before and outside the timed region)
+    tuning = None if args.no_autotune else ctx.autotune(S, m, k)
     clocks = ClockSampler(local)
     clocks.start()
     ms_mixed, L_mixed, steps_mixed = timed(ctx, args.steps, args.warmup, profile=False)
@@ -240,6 +243,12 @@ def run_ours(args):
         barrier()
     h2d = W.n * 4 if Vh is not None else 0
     d2h = S * m * 8 + S * 8 + S * 4
+    # ---- accuracy trial: the same count with the basis rounded to BF16 when stored
+    L_bf16 = None
+    if not args.skip_bf16:
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_BASIS_BF16, 1)
+        _, L_bf16, _ = timed(ctx, 1, 0, profile=False)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_BASIS_BF16, 0)
     ctx.close()
     torch.cuda.empty_cache()
     # ---- FP64 path on the same GPU
@@ -251,6 +260,8 @@ def run_ours(args):
             fp64_note = f"FP64 workspace {need / 1e9:.0f} GB does not fit next to the rest"
         else:
             ctx64 = _make_ctx(evc, W, evc.EVC_FP64, sp)
+            if not args.no_autotune:
+                ctx64.autotune(S, m, k)
             ms_fp64, L_fp64, steps_fp64 = timed(ctx64, max(1, args.steps // 2), 1, profile=False)
             psteps64 = float(m * int(np.sum(steps_fp64)))
             ctx64.close()
@@ -282,7 +293,8 @@ def run_ours(args):
                    "precision": "FP32 vectors/operator, FP64 alpha/beta/reorth coefficients/eig",
                    "step": "one full count: all shifts x probes x executed Lanczos steps",
                    "l2": f"inputs larger than L2 (Lanczos basis {ws_mixed / 1e9:.1f} GB workspace streamed every step)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}",
+                   "tiles": tuning if tuning is not None else "defaults (--no-autotune)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "roofline": roof,
@@ -297,6 +309,13 @@ def run_ours(args):
                      "mixed_minus_fp64": (est_mixed - est_fp64) if est_fp64 is not None else None,
                      "n_below_mixed": [round(float(x), 4) for x in L_mixed],
                      "n_below_fp64": None if L_fp64 is None else [round(float(x), 4) for x in L_fp64]},
+        "bf16_basis": None if L_bf16 is None else {
+            "estimate": float(L_bf16[-1] - L_bf16[0]),
+            "minus_fp64": (float(L_bf16[-1] - L_bf16[0]) - est_fp64) if est_fp64 is not None else None,
+            "minus_mixed": float(L_bf16[-1] - L_bf16[0]) - est_mixed,
+            "n_below": [round(float(x), 4) for x in L_bf16],
+            "note": "basis rounded to BF16 when stored (storage kept FP32): count error of BF16 "
+                    "storage; its traffic would halve the reorthogonalisation bytes"},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_probes, seed=args.seed)
@@ -470,6 +489,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison leg")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg")
+    ap.add_argument("--skip-bf16", action="store_true", help="omit the BF16-basis accuracy trial")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per s")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: server slots")

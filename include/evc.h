@@ -206,14 +206,35 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       one pass per degree moving 4 vectors.  The same operator
  *                       up to rounding.  When the factorisation fails its check
  *                       at EVC_PREC_CHEB_KINETIC time, Clenshaw's recurrence is
- *                       used whatever this option says.  */
+ *                       used whatever this option says.
+ *   EVC_OPT_BASIS_BF16: EVC_MIXED contexts only; 1 rounds every Lanczos basis
+ *                       vector to BF16 (round to nearest even) when it is
+ *                       stored after reorthogonalisation, and takes beta_{i+1}
+ *                       as the norm of the rounded vector: the numerics of a
+ *                       BF16 basis with an FP32 working vector.  The storage
+ *                       itself stays FP32, so this measures the accuracy of
+ *                       BF16 storage, not its bandwidth.  Default 0.
+ *   EVC_OPT_REORTH_ROWS: rows per block of the reorthogonalisation kernels
+ *                       (default 3456, at least 1728).  It sets the summation
+ *                       order of the dot products, so results may change in the
+ *                       last bits; it never depends on how many columns a call
+ *                       batches, so a column's result is the same alone or in
+ *                       a batch for one setting.
+ *   EVC_OPT_STENCIL_ZB: stencil contexts: z planes per block of the stencil
+ *                       pass (default 32).  Results are unchanged.
+ *   EVC_OPT_CSR_THREADS: CSR contexts: threads per block of the CSR pass, 128,
+ *                       256 (default) or 512.  Results are unchanged.  */
 enum {
     EVC_OPT_GRAPH = 1,
     EVC_OPT_PROFILE = 2,
     EVC_OPT_QUADRATURE = 3,
     EVC_OPT_MIN_STEPS = 4,
     EVC_OPT_PROBE_OFFSET = 5,
-    EVC_OPT_CHEB_FORM = 6
+    EVC_OPT_CHEB_FORM = 6,
+    EVC_OPT_BASIS_BF16 = 7,
+    EVC_OPT_REORTH_ROWS = 8,
+    EVC_OPT_STENCIL_ZB = 9,
+    EVC_OPT_CSR_THREADS = 10
 };
 enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };
 enum { EVC_QUAD_GAUSS = 0, EVC_QUAD_GA = 1 };
@@ -246,6 +267,31 @@ typedef struct {
  * (may be NULL) and the number of kernel launches of one call to *nrec.
  * Synchronises the context's stream.                                          */
 int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
+
+/* evc_autotune -- the library's tile-shape autotuner.  Times short counts
+ * (min(maxsteps, 6) Lanczos steps, nshift placeholder shifts, nprobe probes:
+ * the caller's launch shape) with a pair of timing events around every kernel,
+ * and keeps, per kernel family, the fastest of
+ *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB),
+ *   CSR pass:      threads per block 128 / 256 / 512 (EVC_OPT_CSR_THREADS),
+ *   reorthogonalisation: rows per block 1728 / 3456 / 6912 / 13824
+ *                  (EVC_OPT_REORTH_ROWS),
+ * tuning the operator pass first.  The choice stays in the context for later
+ * calls (and contexts cloned from it); `out` (may be NULL) reports it with the
+ * device time of one short count before and after.  Needs the workspace of a
+ * call with (nshift, nprobe, min(maxsteps, 6)) -- a workspace set for the
+ * real call is enough; every configuration fits it.  On error the previous
+ * settings are restored.  Not part of the paper: tile shapes are a property of
+ * the GPU, the grid and the batch. */
+typedef struct {
+    int stencil_zb;      /* chosen z planes per block (stencil contexts), else 0 */
+    int csr_threads;     /* chosen threads per block (CSR contexts), else 0 */
+    int reorth_rows;     /* chosen rows per block of the reorthogonalisation */
+    int steps;           /* Lanczos steps of each timing count */
+    double ms_before;    /* device time of one timing count before tuning */
+    double ms_after;     /* ... and with the chosen shapes */
+} evc_tuning;
+int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning* out);
 
 /* ------------------------------------------------------------------------
  * Request server: interval counts on several resident matrices, served as

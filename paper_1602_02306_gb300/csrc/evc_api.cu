@@ -74,6 +74,8 @@ struct evc_ctx {
     std::vector<ChebFactor> cheb_fac;
     double cheb_g = 1.0, cheb_sign = 1.0;   // |leading coefficient|^(1/d), its sign
     int cheb_form = EVC_CHEB_FACTORED;
+    int basis_bf16 = 0;
+    int reorth_rows = 3456;       // rows per block of the reorthogonalisation kernels
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
     int min_steps = 3;
@@ -134,9 +136,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // column runs alone or batched with others.  3456 rows per block (54 tiles
 // of the update kernel) keeps each block's bulk-copy pipeline long; the
 // 64^3 Hamiltonian with four chunks gets 304 blocks, two per SM.
-int choose_nblk(int64_t n)
+int choose_nblk(int64_t n, int rows = 3456)
 {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 3455) / 3456, 65535));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + rows - 1) / rows, 65535));
 }
 
 struct Layout {
@@ -155,7 +157,8 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     const int ncol_real = S * m;
     const int nchunk = (ncol_real + CW - 1) / CW;
     const int ncol = nchunk * CW;
-    const int nblk = choose_nblk(c->n);
+    const int nblk = choose_nblk(c->n, c->reorth_rows);
+    const int nblk_max = choose_nblk(c->n, kMinReorthRows);   // any tuned value fits
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -200,17 +203,18 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.chunk_active = I(nchunk);
     r.cnt_upd = I(nchunk);
     r.nactive = I(kmax + 1);
-    r.part_dot = D((size_t)nchunk * nblk * kmax * CW);
-    r.part_gram = D((size_t)nchunk * nblk * kmax * CW);
+    r.part_dot = D((size_t)nchunk * nblk_max * kmax * CW);
+    r.part_gram = D((size_t)nchunk * nblk_max * kmax * CW);
     r.hbuf = D((size_t)kmax * ncol);
     r.gram = D((size_t)kmax * (kmax + 1) / 2 * ncol);
-    r.part_nrm = D((size_t)nchunk * nblk * CW);
+    r.part_nrm = D((size_t)nchunk * nblk_max * CW);
     r.err = I(1);
     r.seed = reinterpret_cast<uint64_t*>(take(8));
     r.tol = D(1);
     r.breakdown_rel = c->precision == EVC_FP64 ? 1e-12 : 1e-6;
     r.ga = c->quad_rule == EVC_QUAD_GA ? 1 : 0;
     r.min_steps = c->min_steps;
+    r.basis_bf16 = c->basis_bf16;
     return off;
 }
 
@@ -973,6 +977,8 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->cheb_g = src->cheb_g;
     c->cheb_sign = src->cheb_sign;
     c->cheb_form = src->cheb_form;
+    c->basis_bf16 = src->basis_bf16;
+    c->reorth_rows = src->reorth_rows;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
     c->probe_offset = src->probe_offset;
@@ -1326,6 +1332,40 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         ctx->probe_offset = value;     // a per-call upload, no graph change
         return EVC_OK;
     }
+    if (option == EVC_OPT_REORTH_ROWS) {
+        if (value < kMinReorthRows || value > ((int64_t)1 << 30))
+            return fail(ctx, EVC_EINVAL, "reorthogonalisation rows per block must be >= %d", kMinReorthRows);
+        ctx->reorth_rows = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_STENCIL_ZB) {
+        if (ctx->op != OP_STENCIL) return fail(ctx, EVC_EINVAL, "not a stencil context");
+        if (value < 0 || value > 65536) return fail(ctx, EVC_EINVAL, "z planes per block must be in [0, 65536]");
+        ctx->sten.zb = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_CSR_THREADS) {
+        if (ctx->op != OP_CSR) return fail(ctx, EVC_EINVAL, "not a CSR context");
+        if (value != 128 && value != 256 && value != 512)
+            return fail(ctx, EVC_EINVAL, "CSR threads per block must be 128, 256 or 512");
+        ctx->csr.threads = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_BASIS_BF16) {
+        if (value != 0 && value != 1) return fail(ctx, EVC_EINVAL, "BF16 basis option must be 0 or 1");
+        if (value && ctx->precision != EVC_MIXED)
+            return fail(ctx, EVC_EINVAL, "BF16 basis storage applies to EVC_MIXED contexts only");
+        ctx->basis_bf16 = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
     if (option == EVC_OPT_CHEB_FORM) {
         if (value != EVC_CHEB_FACTORED && value != EVC_CHEB_CLENSHAW)
             return fail(ctx, EVC_EINVAL, "unknown Chebyshev evaluation form %lld", (long long)value);
@@ -1371,6 +1411,113 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec)
         recs[i].ms = ms;
     }
     return EVC_OK;
+}
+
+int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning* out)
+{
+    if (!ctx || nshift < 1 || nprobe < 1 || maxsteps < 1) return EVC_EINVAL;
+    // short counts of the caller's shape (placeholder shifts: the timing of
+    // a fixed number of steps does not depend on them)
+    const int kt = std::min(maxsteps, 6);
+    const std::vector<double> shifts(nshift, 0.0);
+    const bool prof0 = ctx->profile;
+    const int rows0 = ctx->reorth_rows, zb0 = ctx->sten.zb, nt0 = ctx->csr.threads;
+    auto restore = [&](int rc) {
+        ctx->profile = prof0;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        if (rc) {
+            ctx->reorth_rows = rows0;
+            ctx->sten.zb = zb0;
+            ctx->csr.threads = nt0;
+        }
+        return rc;
+    };
+    ctx->profile = true;
+    // device time of the kernel classes in mask (all classes when 0), best of two counts
+    auto measure = [&](unsigned mask, double& ms) -> int {
+        ms = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            ++ctx->prec_version;     // a fresh graph per configuration
+            int rc = evc_count_slices(ctx, shifts.data(), nshift, nprobe, kt, 0.0, 1, nullptr,
+                                      nullptr, nullptr);
+            if (rc) return rc;
+            int nr = 0;
+            evc_get_profile(ctx, nullptr, 0, &nr);
+            std::vector<evc_prof_rec> recs(nr);
+            rc = evc_get_profile(ctx, recs.data(), nr, &nr);
+            if (rc) return rc;
+            double t = 0.0;
+            for (const auto& q : recs)
+                if (q.ms > 0 && (mask == 0 || (mask >> q.kind) & 1u)) t += q.ms;
+            ms = std::min(ms, t);
+        }
+        return EVC_OK;
+    };
+    evc_tuning res{};
+    int rc = measure(0, res.ms_before);
+    if (rc) return restore(rc);
+    // operator pass: z planes per block (stencil) or threads per block (CSR)
+    if (ctx->op == OP_STENCIL) {
+        const int N = ctx->sten.N;
+        std::vector<int> cand;
+        for (int zb : {16, 32, 64}) cand.push_back(std::min(zb, N));
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        double best = 1e300;
+        int bz = cand[0];
+        for (int zb : cand) {
+            ctx->sten.zb = zb;
+            double t;
+            if ((rc = measure(1u << EVC_K_STENCIL, t))) return restore(rc);
+            if (t < best) {
+                best = t;
+                bz = zb;
+            }
+        }
+        ctx->sten.zb = bz;
+    } else {
+        double best = 1e300;
+        int bt = 256;
+        for (int nt : {128, 256, 512}) {
+            ctx->csr.threads = nt;
+            double t;
+            if ((rc = measure(1u << EVC_K_CSR, t))) return restore(rc);
+            if (t < best) {
+                best = t;
+                bt = nt;
+            }
+        }
+        ctx->csr.threads = bt;
+    }
+    // reorthogonalisation: rows per block
+    {
+        double best = 1e300;
+        int br = 3456;
+        int last_nblk = -1;
+        for (int rows : {1728, 3456, 6912, 13824}) {
+            const int nb = choose_nblk(ctx->n, rows);
+            if (nb == last_nblk) continue;
+            last_nblk = nb;
+            ctx->reorth_rows = rows;
+            double t;
+            if ((rc = measure((1u << EVC_K_DOTS) | (1u << EVC_K_REDUCE) | (1u << EVC_K_UPDATE), t)))
+                return restore(rc);
+            if (t < best) {
+                best = t;
+                br = rows;
+            }
+        }
+        ctx->reorth_rows = br;
+    }
+    rc = measure(0, res.ms_after);
+    if (rc) return restore(rc);
+    res.stencil_zb = ctx->op == OP_STENCIL ? ctx->sten.zb : 0;
+    res.csr_threads = ctx->op == OP_CSR ? ctx->csr.threads : 0;
+    res.reorth_rows = ctx->reorth_rows;
+    res.steps = kt;
+    if (out) *out = res;
+    return restore(EVC_OK);
 }
 
 const char* evc_last_error(const evc_ctx* ctx)

@@ -46,8 +46,8 @@ __device__ __forceinline__ Pack<T> ldg16(const T* p)
 // op.perm (rows sorted by length, longest first) so the rows sharing a warp
 // have similar lengths; each group broadcasts the row's (col, val) pairs from
 // its own lanes with warp shuffles.
-template <typename T, bool JAC>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, bool JAC, int NT>
+__global__ void __launch_bounds__(NT)
 csr_pass_kernel(CArgs a)
 {
     constexpr int W = 16 / sizeof(T);
@@ -57,7 +57,7 @@ csr_pass_kernel(CArgs a)
     if (!a.chunk_active[ch]) return;
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPR, sub = lane % LPR;
-    const int64_t slotrow = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * RPW + grp;
+    const int64_t slotrow = ((int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5)) * RPW + grp;
     const int64_t n = a.op.n;
     const bool valid = slotrow < n;
     const int64_t row = valid ? (a.op.perm ? (int64_t)a.op.perm[slotrow] : slotrow) : 0;
@@ -157,10 +157,25 @@ cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, c
     a.jac = r.jac;
     a.chunk_active = r.chunk_active;
     constexpr int RPW = 32 / (CW / (16 / (int)sizeof(T)));
-    const int rows_per_block = (kThreads / 32) * RPW;
+    const int nt = op.threads > 0 ? op.threads : kThreads;
+    const int rows_per_block = (nt / 32) * RPW;
     dim3 grid((unsigned)((op.n + rows_per_block - 1) / rows_per_block), r.nchunk);
-    if (jacobi) csr_pass_kernel<T, true><<<grid, kThreads, 0, st>>>(a);
-    else csr_pass_kernel<T, false><<<grid, kThreads, 0, st>>>(a);
+    switch (nt) {
+    case 128:
+        if (jacobi) csr_pass_kernel<T, true, 128><<<grid, 128, 0, st>>>(a);
+        else csr_pass_kernel<T, false, 128><<<grid, 128, 0, st>>>(a);
+        break;
+    case 256:
+        if (jacobi) csr_pass_kernel<T, true, 256><<<grid, 256, 0, st>>>(a);
+        else csr_pass_kernel<T, false, 256><<<grid, 256, 0, st>>>(a);
+        break;
+    case 512:
+        if (jacobi) csr_pass_kernel<T, true, 512><<<grid, 512, 0, st>>>(a);
+        else csr_pass_kernel<T, false, 512><<<grid, 512, 0, st>>>(a);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ struct Run {
     double breakdown_rel;
     int ga;                  // 1: generalized averaged Gauss quadrature (Sec. 3.4)
     int min_steps;           // no tolerance stop before this step
+    int basis_bf16;          // 1: basis vectors rounded to BF16 when stored (FP32 mode)
 };
 
 // Coefficients of one stencil pass (see evc_stencil.cu):
@@ -95,6 +96,7 @@ struct StencilOp {
     double h;
     double c1, c2, cd;      // L = -1/2 Lap_h: +-1 neighbours, +-2 neighbours, diagonal
     const void* V;          // T[n]
+    int zb;                 // z planes per block (tuned; 0 = 32)
 };
 
 struct CsrOp {
@@ -104,7 +106,12 @@ struct CsrOp {
     const void* val;        // T[nnz]
     const double* diag;     // double[n]
     const int32_t* perm;    // [n] rows by decreasing length (visit order), or null
+    int threads;            // threads per block: 128, 256 (default) or 512 (tuned)
 };
+
+// Smallest rows-per-block of the reorthogonalisation kernels that a tuned
+// context may use; the workspace sizes the per-block partial sums for it.
+constexpr int kMinReorthRows = 1728;
 
 // Kernel launchers (T = float for EVC_MIXED, double for EVC_FP64).
 template <typename T>

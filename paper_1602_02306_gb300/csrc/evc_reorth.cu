@@ -30,6 +30,8 @@
 #include "evc_tridiag.cuh"
 #include "evc_bulk.cuh"
 
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 namespace evc {
@@ -461,6 +463,10 @@ reorth_update_kernel(Run r, int i)
             for (int rr = 0; rr < RPW; ++rr) {
                 const int row = warp * RPW + rr;
                 if (row < rows) {
+                    // BF16 storage of the basis (an accuracy trial): the vector
+                    // kept is the rounded one, and beta is its norm
+                    if (sizeof(T) == 4 && r.basis_bf16)
+                        wv[rr] = (T)__bfloat162float(__float2bfloat16_rn((float)wv[rr]));
                     w[(row0 + row) * CW + lane] = wv[rr];
                     nr += (RTy)wv[rr] * (RTy)wv[rr];
                 }

@@ -54,7 +54,7 @@ __device__ __forceinline__ void st_pack(Pack<T>* p, const Pack<T>& v)
     *reinterpret_cast<typename Vec16<T>::type*>(p) = t;
 }
 
-constexpr int ZB = 32;     // z planes per block
+constexpr int ZB = 32;     // z planes per block unless tuned (StencilOp::zb)
 constexpr int STH = 128;   // threads per block
 constexpr int DEPTH = 3;   // planes of loads in flight ahead of the one computed
 
@@ -121,8 +121,9 @@ stencil_pass_kernel(KArgs a)
     const int x = (blockIdx.x % tilesX) * TX + pt % TX;
     const int y = (blockIdx.x / tilesX) * TY + pt / TX;
     if (x >= N || y >= N) return;            // no block-level barriers below
-    const int z0 = blockIdx.y * ZB;
-    const int z1 = min(z0 + ZB, N);
+    const int zb = a.op.zb > 0 ? a.op.zb : ZB;
+    const int z0 = blockIdx.y * zb;
+    const int z1 = min(z0 + zb, N);
     const int64_t n = a.n;
     const int64_t NN = (int64_t)N * N;
 
@@ -318,7 +319,8 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     a.chunk_active = r.chunk_active;
     a.n = r.n;
     const int N = op.N;
-    dim3 grid(((N + TX - 1) / TX) * ((N + TY - 1) / TY), (N + ZB - 1) / ZB, r.nchunk);
+    const int zb = op.zb > 0 ? op.zb : ZB;
+    dim3 grid(((N + TX - 1) / TX) * ((N + TY - 1) / TY), (N + zb - 1) / zb, r.nchunk);
     // V and the per-column shift always enter together (the H - sigma I pass)
     if (p.useV != p.useSigma) return cudaErrorInvalidValue;
     const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |

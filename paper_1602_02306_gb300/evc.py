@@ -28,6 +28,8 @@ EVC_FP64, EVC_MIXED = 0, 1
 EVC_PREC_IDENTITY, EVC_PREC_JACOBI, EVC_PREC_CHEB_KINETIC = 0, 1, 2
 EVC_OPT_GRAPH, EVC_OPT_PROFILE, EVC_OPT_QUADRATURE, EVC_OPT_MIN_STEPS, EVC_OPT_PROBE_OFFSET = 1, 2, 3, 4, 5
 EVC_OPT_CHEB_FORM = 6
+EVC_OPT_BASIS_BF16 = 7
+EVC_OPT_REORTH_ROWS, EVC_OPT_STENCIL_ZB, EVC_OPT_CSR_THREADS = 8, 9, 10
 EVC_CHEB_FACTORED, EVC_CHEB_CLENSHAW = 0, 1
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1
 (EVC_K_INIT, EVC_K_JACOBI, EVC_K_STENCIL, EVC_K_CSR, EVC_K_DOTS, EVC_K_REDUCE, EVC_K_UPDATE,
@@ -40,7 +42,7 @@ EXPORTED = [
     "evc_create_csr", "evc_create_stencil", "evc_set_values", "evc_set_precond",
     "evc_workspace_bytes", "evc_set_workspace", "evc_count", "evc_count_slices",
     "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_set_option",
-    "evc_get_profile", "evc_server_create", "evc_server_add_matrix", "evc_server_submit",
+    "evc_get_profile", "evc_autotune", "evc_server_create", "evc_server_add_matrix", "evc_server_submit",
     "evc_server_poll", "evc_server_wait", "evc_server_stats", "evc_server_destroy",
     "evc_gauss_quadrature_static", "evc_last_error", "evc_destroy", "evc_version",
 ]
@@ -60,6 +62,11 @@ class evc_csr(C.Structure):
 
 class evc_prof_rec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("step", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+class evc_tuning(C.Structure):
+    _fields_ = [("stencil_zb", C.c_int), ("csr_threads", C.c_int), ("reorth_rows", C.c_int),
+                ("steps", C.c_int), ("ms_before", C.c_double), ("ms_after", C.c_double)]
 
 
 class evc_result(C.Structure):
@@ -104,6 +111,7 @@ def load(path: str | None = None):
             "evc_count_slices_async": (i32, [vp, dp, i32, i32, i32, d, u64, vp, vp, vp]),
             "evc_sync": (i32, [vp]),
             "evc_get_tridiag": (i32, [vp, dp, dp, ip]),
+            "evc_autotune": (i32, [vp, i32, i32, i32, C.POINTER(evc_tuning)]),
             "evc_set_option": (i32, [vp, i32, i64]),
             "evc_get_profile": (i32, [vp, C.POINTER(evc_prof_rec), i32, ip]),
             "evc_server_create": (i32, [C.c_size_t, i32, i32, pp]),
@@ -242,6 +250,13 @@ def evc_set_option(ctx, option, value):
     _check(ctx, load().evc_set_option(ctx, option, int(value)))
 
 
+def evc_autotune(ctx, nshift, nprobe, maxsteps):
+    """Pick the kernels' tile shapes for this launch shape; returns the choice."""
+    t = evc_tuning()
+    _check(ctx, load().evc_autotune(ctx, nshift, nprobe, maxsteps, C.byref(t)))
+    return {f: getattr(t, f) for f, _ in evc_tuning._fields_}
+
+
 def evc_get_profile(ctx):
     """Launch list of the last call: list of (kind, step, ms, bytes)."""
     lib = load()
@@ -361,6 +376,9 @@ class Context:
     def set_option(self, option, value):
         evc_set_option(self.h, option, value)
         return self
+
+    def autotune(self, nshift, nprobe, maxsteps):
+        return evc_autotune(self.h, nshift, nprobe, maxsteps)
 
     def reserve(self, nshift, nprobe, maxsteps):
         """Allocate the library's scratch from the torch caching allocator."""

@@ -1,0 +1,98 @@
+"""The tile-shape parameters and the autotuner that picks them: shapes that
+do not touch the arithmetic leave results bitwise unchanged, the rows per
+block of the reorthogonalisation only reorders sums, and a tuned context
+still matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1602_02306_gb300 import evc
+from paper_1602_02306_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_02306_gb300 import build
+    build.build()
+    evc.load()
+
+
+def _stencil_ctx(N, prec=evc.EVC_FP64):
+    V = I.gaussian_wells(N, 0.3, nwells=5, seed=1)
+    ctx = evc.Context.stencil(N, 0.3, 2, V, precision=prec)
+    ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, 8, 1.0)
+    return V, ctx
+
+
+def test_stencil_zb_leaves_results_unchanged():
+    shifts, m, k = [-2.0, 0.5], 40, 8
+    V, ctx = _stencil_ctx(37)
+    with ctx:
+        ref = ctx.count_slices(shifts, m, k)[1]
+        for zb in (1, 5, 16, 64, 100):
+            ctx.set_option(evc.EVC_OPT_STENCIL_ZB, zb)
+            np.testing.assert_array_equal(ctx.count_slices(shifts, m, k)[1], ref)
+
+
+def test_csr_threads_leave_results_unchanged():
+    csr = I.powerlaw_symmetric(20000, cap=300, seed=2)
+    with evc.Context.csr(csr, precision=evc.EVC_FP64) as ctx:
+        ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        ref = ctx.count_slices([-0.5, 0.5], 33, 10)[1]
+        for nt in (128, 512, 256):
+            ctx.set_option(evc.EVC_OPT_CSR_THREADS, nt)
+            np.testing.assert_array_equal(ctx.count_slices([-0.5, 0.5], 33, 10)[1], ref)
+
+
+def test_reorth_rows_reorder_sums_only():
+    shifts, m, k = [-2.5, 0.5], 36, 12
+    V, ctx = _stencil_ctx(25)
+    P = O.Problem.stencil(25, 0.3, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
+    qr, _, _ = O.count(P, shifts, m, k, seed=0)
+    with ctx:
+        for rows in (1728, 3456, 6912, 100000):
+            ctx.set_option(evc.EVC_OPT_REORTH_ROWS, rows)
+            q = ctx.count_slices(shifts, m, k)[1]
+            assert np.max(np.abs(q - qr)) < 1e-8
+
+
+def test_autotune_choices_and_parity():
+    shifts, m, k = [-2.5, 0.5], 40, 10
+    V, ctx = _stencil_ctx(30)
+    with ctx:
+        t = ctx.autotune(len(shifts), m, k)
+        assert t["stencil_zb"] in (16, 30) and t["csr_threads"] == 0
+        assert t["reorth_rows"] in (1728, 3456, 6912, 13824)
+        assert t["ms_before"] > 0 and t["ms_after"] > 0 and t["steps"] == 6
+        q = ctx.count_slices(shifts, m, k)[1]
+    P = O.Problem.stencil(30, 0.3, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
+    qr, _, _ = O.count(P, shifts, m, k, seed=0)
+    assert np.max(np.abs(q - qr)) < 1e-8
+
+
+def test_autotune_csr_and_batch_independence():
+    csr = I.powerlaw_symmetric(30000, cap=300, seed=2)
+    with evc.Context.csr(csr, precision=evc.EVC_MIXED) as ctx:
+        ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        t = ctx.autotune(3, 32, 12)
+        assert t["csr_threads"] in (128, 256, 512) and t["stencil_zb"] == 0
+        # a column's result is the same alone and batched, with the tuned shapes
+        q1 = ctx.count_slices([0.1], 32, 12)[1]
+        q3 = ctx.count_slices([-0.4, 0.1, 0.3], 32, 12)[1]
+    np.testing.assert_array_equal(q1[0], q3[1])
+
+
+def test_tuning_options_validate():
+    V, ctx = _stencil_ctx(8)
+    with ctx:
+        for opt, bad in ((evc.EVC_OPT_REORTH_ROWS, 1000), (evc.EVC_OPT_STENCIL_ZB, -1),
+                         (evc.EVC_OPT_CSR_THREADS, 256)):
+            with pytest.raises(evc.EvcError):
+                ctx.set_option(opt, bad)
+        with pytest.raises(evc.EvcError):
+            ctx.autotune(0, 8, 4)

@@ -70,3 +70,25 @@ def test_cheb_form_option_validates():
     with evc.Context.stencil(8, 0.3, 2, V, precision=evc.EVC_FP64) as ctx:
         with pytest.raises(evc.EvcError):
             ctx.set_option(evc.EVC_OPT_CHEB_FORM, 2)
+
+
+def test_bf16_basis_option():
+    # accuracy trial: a BF16-rounded basis changes the estimate by far less
+    # than the Hutchinson error but is not the FP32 result; FP64 contexts refuse it
+    N, shifts, m, k = 16, [-3.0, 1.0], 64, 20
+    V = I.gaussian_wells(N, 0.3, nwells=5, seed=1)
+    with evc.Context.stencil(N, 0.3, 2, V, precision=evc.EVC_MIXED) as ctx:
+        ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, 8, 1.0)
+        L32, q32, _ = ctx.count_slices(shifts, m, k, seed=0)
+        ctx.set_option(evc.EVC_OPT_BASIS_BF16, 1)
+        L16, q16, _ = ctx.count_slices(shifts, m, k, seed=0)
+        ctx.set_option(evc.EVC_OPT_BASIS_BF16, 0)
+        L32b, _, _ = ctx.count_slices(shifts, m, k, seed=0)
+    np.testing.assert_array_equal(L32, L32b)
+    assert not np.array_equal(q32, q16)
+    assert np.all(np.isfinite(q16))
+    assert np.max(np.abs(L16 - L32)) < 2.0
+    with evc.Context.stencil(8, 0.3, 2, I.gaussian_wells(8, 0.3, nwells=2, seed=1),
+                             precision=evc.EVC_FP64) as ctx:
+        with pytest.raises(evc.EvcError):
+            ctx.set_option(evc.EVC_OPT_BASIS_BF16, 1)
