@@ -94,6 +94,7 @@ class ClockSampler:
 
 
 _CHEB_FORM = [0]     # EVC_CHEB_FACTORED; --cheb-form clenshaw sets 1
+_METHOD = [0]        # EVC_METHOD_LANCZOS; --method arnoldi sets 1
 
 
 def _make_ctx(evc, W, precision, stream_ptr, V=None):
@@ -108,6 +109,7 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
     evc.evc_set_option(ctx.h, evc.EVC_OPT_MIN_STEPS, W.min_steps)
     if W.precond == "cheb":
         evc.evc_set_option(ctx.h, evc.EVC_OPT_CHEB_FORM, _CHEB_FORM[0])
+    evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, _METHOD[0])
     ctx.reserve(len(W.shifts), W.nprobe, W.maxsteps)
     return ctx
 
@@ -294,6 +296,7 @@ def run_ours(args):
                    "step": "one full count: all shifts x probes x executed Lanczos steps",
                    "l2": f"inputs larger than L2 (Lanczos basis {ws_mixed / 1e9:.1f} GB workspace streamed every step)",
                    "parallelism": f"replicas{world}",
+                   "method": ["lanczos (Algorithms 1-2)", "arnoldi (Sec. 4, Algorithm 3)"][_METHOD[0]],
                    "tiles": tuning if tuning is not None else "defaults (--no-autotune)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
@@ -338,8 +341,15 @@ def cpu_baseline(W, nprobe_sample, seed=0):
         pk = {"identity": O.PREC_NONE, "jacobi": O.PREC_JACOBI}[W.precond]
         P = O.Problem.csr_matrix(W.csr(), pk, jac_eps=float(W.prec_params[0]))
     t0 = time.perf_counter()
-    q, st, L = O.count(P, W.shifts, nprobe_sample, W.maxsteps, tol=W.tol, seed=seed,
-                       nthreads=cores)
+    if _METHOD[0] == 1:
+        # the Arnoldi oracle is numpy on one core: a quarter of the sample
+        from oracle import arnoldi as AR
+        nprobe_sample = max(1, nprobe_sample // 4)
+        cores = 1
+        q, st, L = AR.count(P, W.shifts, nprobe_sample, W.maxsteps, tol=W.tol, seed=seed)
+    else:
+        q, st, L = O.count(P, W.shifts, nprobe_sample, W.maxsteps, tol=W.tol, seed=seed,
+                           nthreads=cores)
     dt = time.perf_counter() - t0
     ps = float(len(W.shifts) * nprobe_sample * W.maxsteps)
     return {"value": round(ps / dt, 2), "unit": UNIT, "cores": min(cores, len(W.shifts) * nprobe_sample),
@@ -491,6 +501,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg")
     ap.add_argument("--skip-bf16", action="store_true", help="omit the BF16-basis accuracy trial")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
+    ap.add_argument("--method", default="lanczos", choices=["lanczos", "arnoldi"],
+                    help="estimator: preconditioned Lanczos (default) or the Arnoldi-type variant")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per s")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: server slots")
@@ -498,6 +510,7 @@ def main():
                     help="how the Chebyshev preconditioner polynomial is applied")
     args = ap.parse_args()
     _CHEB_FORM[0] = 0 if args.cheb_form == "factored" else 1
+    _METHOD[0] = 0 if args.method == "lanczos" else 1
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":

@@ -223,7 +223,18 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *   EVC_OPT_STENCIL_ZB: stencil contexts: z planes per block of the stencil
  *                       pass (default 32).  Results are unchanged.
  *   EVC_OPT_CSR_THREADS: CSR contexts: threads per block of the CSR pass, 128,
- *                       256 (default) or 512.  Results are unchanged.  */
+ *                       256 (default) or 512.  Results are unchanged.
+ *   EVC_OPT_METHOD    : EVC_METHOD_LANCZOS (default): Algorithms 1-2 on
+ *                       C = M (A - tau I) M.  EVC_METHOD_ARNOLDI: the
+ *                       preconditioned Arnoldi-type estimator of Sec. 4 -- the
+ *                       Arnoldi process (Algorithm 3) on C = T (A - tau I) with T
+ *                       used without its factorisation (Jacobi: T = diag(1/(|a_ii
+ *                       - tau| + eps)); Chebyshev: T = p_d(K)^2; identity), the
+ *                       quadrature ||v||^2 Re(e_1^T h(H_k) e_1) with h = 1 on the
+ *                       open left half-plane (Eq. arnoldi_quad), the same probes,
+ *                       means and stop rule.  At most 64 steps; the Gauss rule
+ *                       only; evc_get_tridiag does not apply.  Per-probe values
+ *                       may be negative (the weights are complex).  */
 enum {
     EVC_OPT_GRAPH = 1,
     EVC_OPT_PROFILE = 2,
@@ -234,8 +245,10 @@ enum {
     EVC_OPT_BASIS_BF16 = 7,
     EVC_OPT_REORTH_ROWS = 8,
     EVC_OPT_STENCIL_ZB = 9,
-    EVC_OPT_CSR_THREADS = 10
+    EVC_OPT_CSR_THREADS = 10,
+    EVC_OPT_METHOD = 11
 };
+enum { EVC_METHOD_LANCZOS = 0, EVC_METHOD_ARNOLDI = 1 };
 enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };
 enum { EVC_QUAD_GAUSS = 0, EVC_QUAD_GA = 1 };
 int evc_set_option(evc_ctx* ctx, int option, int64_t value);

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libevc.so")
-SOURCES = ["evc_api.cu", "evc_stencil.cu", "evc_csr.cu", "evc_reorth.cu", "evc_static.cu",
-           "evc_server.cu"]
+SOURCES = ["evc_api.cu", "evc_stencil.cu", "evc_csr.cu", "evc_reorth.cu", "evc_arnoldi.cu",
+           "evc_static.cu", "evc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -76,6 +76,7 @@ struct evc_ctx {
     int cheb_form = EVC_CHEB_FACTORED;
     int basis_bf16 = 0;
     int reorth_rows = 3456;       // rows per block of the reorthogonalisation kernels
+    int method = EVC_METHOD_LANCZOS;
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
     int min_steps = 3;
@@ -215,6 +216,8 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.ga = c->quad_rule == EVC_QUAD_GA ? 1 : 0;
     r.min_steps = c->min_steps;
     r.basis_bf16 = c->basis_bf16;
+    r.arnoldi = c->method == EVC_METHOD_ARNOLDI ? 1 : 0;
+    r.hess = r.arnoldi ? D((size_t)kmax * (kmax + 1) / 2 * ncol) : nullptr;
     return off;
 }
 
@@ -633,6 +636,54 @@ int enqueue_cheb(evc_ctx* ctx, const Run& r, int step, const void* x, int64_t x_
     return EVC_OK;
 }
 
+// Arnoldi (Sec. 4, Algorithm 3): w = T (A - sigma I) q_i into slot i, with T
+// used without its factorisation and no three-term term.  Chebyshev:
+// T = p_d(K)^2, i.e. (H - sigma I) into slot i, M into W2, M back into slot i;
+// Jacobi: T = diag(m^2) as a row scaling after the plain operator pass.
+template <typename T>
+int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
+{
+    cudaStream_t st = ctx->stream;
+    const double vchunk = (double)r.n * CW * sizeof(T);
+    T* basis = static_cast<T*>(r.basis);
+    T* qi = basis + (int64_t)(i - 1) * r.slot_stride;
+    T* wout = basis + (int64_t)i * r.slot_stride;
+    const double* si = r.scl + (int64_t)(i - 1) * r.ncol;
+    const int64_t vstride = r.n * CW;
+    int rc;
+    if (ctx->op == OP_CSR) {
+        const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1);
+        const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk;
+        rc = rec(ctx, EVC_K_CSR, i, fixed, per,
+                 [&] { return launch_csr_pass<T>(ctx->csr, r, i, false, st); });
+    } else {
+        StencilPass p{};
+        p.in = qi;
+        p.in_cs = r.chunk_stride;
+        p.insc = si;
+        p.k1 = 1.0;
+        p.useV = 1;
+        p.useSigma = 1;
+        p.out = wout;
+        p.out_cs = r.chunk_stride;
+        rc = stencil<T>(ctx, r, i, p, false);
+        if (!rc && ctx->prec == EVC_PREC_CHEB_KINETIC) {
+            T* W0 = static_cast<T*>(work);
+            T* W1 = W0 + (int64_t)r.nchunk * vstride;
+            T* W2 = W1 + (int64_t)r.nchunk * vstride;
+            rc = enqueue_cheb<T>(ctx, r, i, wout, r.chunk_stride, nullptr, W0, W1, W2, vstride,
+                                 nullptr, 0, nullptr);
+            if (!rc)
+                rc = enqueue_cheb<T>(ctx, r, i, W2, vstride, nullptr, W0, W1, wout, r.chunk_stride,
+                                     nullptr, 0, nullptr);
+        }
+    }
+    if (!rc && uses_jac(ctx))
+        rc = rec(ctx, EVC_K_JACOBI, i, (double)r.S * r.n * sizeof(T), 2.0 * vchunk,
+                 [&] { return launch_row_scale<T>(r, wout, r.chunk_stride, st); });
+    return rc;
+}
+
 template <typename T>
 int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
 {
@@ -657,7 +708,9 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         T* qprev = i >= 2 ? basis + (int64_t)(i - 2) * r.slot_stride : nullptr;
         T* wout = basis + (int64_t)i * r.slot_stride;
         const double* si = r.scl + (int64_t)(i - 1) * r.ncol;
-        if (ctx->op == OP_CSR) {
+        if (r.arnoldi) {
+            rc = enqueue_arnoldi_operator<T>(ctx, r, i, work);
+        } else if (ctx->op == OP_CSR) {
             // the CSR structure and values once; per chunk, one gathered 32-column
             // x row per stored entry, the output and q_{i-1}
             const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
@@ -762,6 +815,13 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
         if (!std::isfinite(shifts[s])) return fail(ctx, EVC_EINVAL, "shift %d is not finite", s);
     if (!std::isfinite(tol)) return fail(ctx, EVC_EINVAL, "tol is not finite");
     const int kmax = (int)std::min<int64_t>(maxsteps, ctx->n);
+    if (ctx->method == EVC_METHOD_ARNOLDI) {
+        if (kmax > kArnoldiMaxSteps)
+            return fail(ctx, EVC_EINVAL, "the Arnoldi method runs at most %d steps (got %d)",
+                        kArnoldiMaxSteps, kmax);
+        if (ctx->quad_rule != EVC_QUAD_GAUSS)
+            return fail(ctx, EVC_EUNSUPPORTED, "the averaged Gauss rule is a Lanczos quadrature");
+    }
     Layout L = layout(ctx, S, m, kmax);
     if (L.total > ctx->ws_bytes) {
         if (!ctx->ws_owned && ctx->ws)
@@ -979,6 +1039,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->cheb_form = src->cheb_form;
     c->basis_bf16 = src->basis_bf16;
     c->reorth_rows = src->reorth_rows;
+    c->method = src->method;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
     c->probe_offset = src->probe_offset;
@@ -1283,6 +1344,8 @@ int evc_count(evc_ctx* ctx, double xi, double eta, int nprobe, int maxsteps, dou
 
 int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone)
 {
+    if (ctx && ctx->have_run && ctx->run.arnoldi)
+        return fail(ctx, EVC_EUNSUPPORTED, "the last call ran the Arnoldi method: no tridiagonal");
     if (!ctx) return EVC_EINVAL;
     if (!ctx->have_run) return fail(ctx, EVC_EINVAL, "no previous run");
     const Run& r = ctx->run;
@@ -1330,6 +1393,14 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         if (value < 0 || value > ((int64_t)1 << 31))
             return fail(ctx, EVC_EINVAL, "probe offset must be in [0, 2^31]");
         ctx->probe_offset = value;     // a per-call upload, no graph change
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_METHOD) {
+        if (value != EVC_METHOD_LANCZOS && value != EVC_METHOD_ARNOLDI)
+            return fail(ctx, EVC_EINVAL, "unknown method %lld", (long long)value);
+        ctx->method = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
         return EVC_OK;
     }
     if (option == EVC_OPT_REORTH_ROWS) {

@@ -147,7 +147,8 @@ cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, c
     a.op = op;
     T* basis = static_cast<T*>(r.basis);
     a.x = basis + (int64_t)(i - 1) * r.slot_stride;
-    a.pp = i >= 2 ? basis + (int64_t)(i - 2) * r.slot_stride : nullptr;
+    // the three-term term -beta_i q_{i-1} is Lanczos only
+    a.pp = (i >= 2 && !r.arnoldi) ? basis + (int64_t)(i - 2) * r.slot_stride : nullptr;
     a.out = basis + (int64_t)i * r.slot_stride;
     a.chunk_stride = r.chunk_stride;
     a.insc = r.scl + (int64_t)(i - 1) * r.ncol;

@@ -72,7 +72,13 @@ struct Run {
     int ga;                  // 1: generalized averaged Gauss quadrature (Sec. 3.4)
     int min_steps;           // no tolerance stop before this step
     int basis_bf16;          // 1: basis vectors rounded to BF16 when stored (FP32 mode)
+    int arnoldi;             // 1: Arnoldi process on T(A - sigma I) (Sec. 4)
+    double* hess;            // [kmax(kmax+1)/2][ncol] Hessenberg columns (Arnoldi), or null
 };
+
+// Longest Arnoldi run: the quadrature keeps three k x k FP64 matrices in
+// shared memory (evc_arnoldi.cu).
+constexpr int kArnoldiMaxSteps = 64;
 
 // Coefficients of one stencil pass (see evc_stencil.cu):
 //   st  = k1 * (L in)_offdiag + (k1*cd + k0 + [V_p] - [sigma_c]) * in_p
@@ -117,6 +123,10 @@ constexpr int kMinReorthRows = 1728;
 template <typename T>
 cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const StencilPass& p,
                                 bool jacobi, cudaStream_t st);
+// Arnoldi-type estimator (evc_arnoldi.cu)
+template <typename T>
+cudaError_t launch_row_scale(const Run& r, void* w, int64_t cs, cudaStream_t st);
+cudaError_t launch_arnoldi_quad(const Run& r, int i, cudaStream_t st);
 template <typename T>
 cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, cudaStream_t st);
 cudaError_t launch_init_state(const Run& r, cudaStream_t st);

@@ -347,6 +347,8 @@ __global__ void reorth_coef_kernel(Run r, int i)
     }
     const double hj = r.hbuf[(int64_t)j * r.ncol + c];
     r.g[(int64_t)j * r.ncol + c] = (2.0 * hj - gh) * r.scl[(int64_t)j * r.ncol + c];
+    // Arnoldi: the full coefficient is the Hessenberg entry h_{j+1,i} (Algorithm 3)
+    if (r.hess) r.hess[tri(i - 1, j) * r.ncol + c] = 2.0 * hj - gh;
 }
 
 // w <- w - sum_{j<i} g_j P_j (in place, slot i); part_nrm = partial ||w||^2.
@@ -729,7 +731,12 @@ cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st)
         cudaFuncSetAttribute(quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         attr_set = true;
     }
-    quad_kernel<<<(r.ncol_real + qb - 1) / qb, qb, smem, st>>>(r, i);
+    if (r.arnoldi) {
+        const cudaError_t e = launch_arnoldi_quad(r, i, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        quad_kernel<<<(r.ncol_real + qb - 1) / qb, qb, smem, st>>>(r, i);
+    }
     shift_kernel<<<r.S, kThreads, 0, st>>>(r, i, last ? 1 : 0);
     return cudaGetLastError();
 }

@@ -30,6 +30,8 @@ EVC_OPT_GRAPH, EVC_OPT_PROFILE, EVC_OPT_QUADRATURE, EVC_OPT_MIN_STEPS, EVC_OPT_P
 EVC_OPT_CHEB_FORM = 6
 EVC_OPT_BASIS_BF16 = 7
 EVC_OPT_REORTH_ROWS, EVC_OPT_STENCIL_ZB, EVC_OPT_CSR_THREADS = 8, 9, 10
+EVC_OPT_METHOD = 11
+EVC_METHOD_LANCZOS, EVC_METHOD_ARNOLDI = 0, 1
 EVC_CHEB_FACTORED, EVC_CHEB_CLENSHAW = 0, 1
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1
 (EVC_K_INIT, EVC_K_JACOBI, EVC_K_STENCIL, EVC_K_CSR, EVC_K_DOTS, EVC_K_REDUCE, EVC_K_UPDATE,
