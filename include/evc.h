@@ -222,6 +222,11 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       a batch for one setting.
  *   EVC_OPT_STENCIL_ZB: stencil contexts: z planes per block of the stencil
  *                       pass (default 32).  Results are unchanged.
+ *   EVC_OPT_STENCIL_PATCH: stencil contexts: points per thread of the stencil
+ *                       pass, 1 (default) or 2 = a 2 x 2 patch of (x, y) points
+ *                       whose inner neighbours come from registers (fewer loads
+ *                       per output; passes without Jacobi scaling and grids
+ *                       with N even, else 1 is used).  Results agree to rounding.
  *   EVC_OPT_CSR_THREADS: CSR contexts: threads per block of the CSR pass, 128,
  *                       256 (default) or 512.  Results are unchanged.
  *   EVC_OPT_METHOD    : EVC_METHOD_LANCZOS (default): Algorithms 1-2 on
@@ -246,7 +251,8 @@ enum {
     EVC_OPT_REORTH_ROWS = 8,
     EVC_OPT_STENCIL_ZB = 9,
     EVC_OPT_CSR_THREADS = 10,
-    EVC_OPT_METHOD = 11
+    EVC_OPT_METHOD = 11,
+    EVC_OPT_STENCIL_PATCH = 12
 };
 enum { EVC_METHOD_LANCZOS = 0, EVC_METHOD_ARNOLDI = 1 };
 enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };
@@ -285,7 +291,8 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  * (min(maxsteps, 6) Lanczos steps, nshift placeholder shifts, nprobe probes:
  * the caller's launch shape) with a pair of timing events around every kernel,
  * and keeps, per kernel family, the fastest of
- *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB),
+ *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB) times
+ *                  points per thread 1 / 2x2 (EVC_OPT_STENCIL_PATCH),
  *   CSR pass:      threads per block 128 / 256 / 512 (EVC_OPT_CSR_THREADS),
  *   reorthogonalisation: rows per block 1728 / 3456 / 6912 / 13824
  *                  (EVC_OPT_REORTH_ROWS),
@@ -298,6 +305,7 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  * the GPU, the grid and the batch. */
 typedef struct {
     int stencil_zb;      /* chosen z planes per block (stencil contexts), else 0 */
+    int stencil_patch;   /* chosen points per thread, 1 or 2 (2 x 2 patch), else 0 */
     int csr_threads;     /* chosen threads per block (CSR contexts), else 0 */
     int reorth_rows;     /* chosen rows per block of the reorthogonalisation */
     int steps;           /* Lanczos steps of each timing count */

@@ -1419,6 +1419,14 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         drop_graph(ctx);
         return EVC_OK;
     }
+    if (option == EVC_OPT_STENCIL_PATCH) {
+        if (ctx->op != OP_STENCIL) return fail(ctx, EVC_EINVAL, "not a stencil context");
+        if (value != 1 && value != 2) return fail(ctx, EVC_EINVAL, "stencil patch must be 1 or 2");
+        ctx->sten.patch = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
     if (option == EVC_OPT_CSR_THREADS) {
         if (ctx->op != OP_CSR) return fail(ctx, EVC_EINVAL, "not a CSR context");
         if (value != 128 && value != 256 && value != 512)
@@ -1492,7 +1500,8 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
     const int kt = std::min(maxsteps, 6);
     const std::vector<double> shifts(nshift, 0.0);
     const bool prof0 = ctx->profile;
-    const int rows0 = ctx->reorth_rows, zb0 = ctx->sten.zb, nt0 = ctx->csr.threads;
+    const int rows0 = ctx->reorth_rows, zb0 = ctx->sten.zb, nt0 = ctx->csr.threads,
+              pa0 = ctx->sten.patch;
     auto restore = [&](int rc) {
         ctx->profile = prof0;
         ++ctx->prec_version;
@@ -1500,6 +1509,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
         if (rc) {
             ctx->reorth_rows = rows0;
             ctx->sten.zb = zb0;
+            ctx->sten.patch = pa0;
             ctx->csr.threads = nt0;
         }
         return rc;
@@ -1536,17 +1546,23 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
         std::sort(cand.begin(), cand.end());
         cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
         double best = 1e300;
-        int bz = cand[0];
-        for (int zb : cand) {
-            ctx->sten.zb = zb;
-            double t;
-            if ((rc = measure(1u << EVC_K_STENCIL, t))) return restore(rc);
-            if (t < best) {
-                best = t;
-                bz = zb;
+        int bz = cand[0], bp = 1;
+        for (int pa : {1, 2}) {
+            if (pa == 2 && N % 2) continue;
+            for (int zb : cand) {
+                ctx->sten.zb = zb;
+                ctx->sten.patch = pa;
+                double t;
+                if ((rc = measure(1u << EVC_K_STENCIL, t))) return restore(rc);
+                if (t < best) {
+                    best = t;
+                    bz = zb;
+                    bp = pa;
+                }
             }
         }
         ctx->sten.zb = bz;
+        ctx->sten.patch = bp;
     } else {
         double best = 1e300;
         int bt = 256;
@@ -1584,6 +1600,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
     rc = measure(0, res.ms_after);
     if (rc) return restore(rc);
     res.stencil_zb = ctx->op == OP_STENCIL ? ctx->sten.zb : 0;
+    res.stencil_patch = ctx->op == OP_STENCIL ? std::max(1, ctx->sten.patch) : 0;
     res.csr_threads = ctx->op == OP_CSR ? ctx->csr.threads : 0;
     res.reorth_rows = ctx->reorth_rows;
     res.steps = kt;

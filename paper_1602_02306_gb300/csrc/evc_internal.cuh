@@ -103,6 +103,7 @@ struct StencilOp {
     double c1, c2, cd;      // L = -1/2 Lap_h: +-1 neighbours, +-2 neighbours, diagonal
     const void* V;          // T[n]
     int zb;                 // z planes per block (tuned; 0 = 32)
+    int patch;              // points per thread: 1 (default) or 2 = a 2 x 2 patch (tuned)
 };
 
 struct CsrOp {

@@ -262,6 +262,244 @@ stencil_pass_kernel(KArgs a)
     cp_async_wait<0>();
 }
 
+// Patch variant of the same pass (no Jacobi scaling): each thread owns the
+// same 16-byte column vector of a PX x PY patch of (x, y) points and marches
+// them along z together.  Neighbours that fall inside the patch come from the
+// thread's own register window; only the 2R(PX + PY) points around the patch
+// are loaded.  The pass is bound by the L1 pipe (one cp.async and one
+// shared-memory read per loaded vector), so a 2 x 2 patch cuts the loads per
+// output of the 7-point stencil from 4R + 1 to R(PX + PY)/2 + 1 plus the
+// pointwise operands.  Per-point arithmetic and summation order are those of
+// stencil_pass_kernel.  N must be a multiple of PX and PY.
+constexpr int STP = 64;    // threads per block of the patch variant
+
+template <typename T, int R, int MASK, int PX, int PY>
+__global__ void __launch_bounds__(STP)
+stencil_patch_kernel(KArgs a)
+{
+    constexpr int W = 16 / sizeof(T);
+    constexpr int LPP = CW / W;
+    constexpr int NPT = PX * PY;                 // points per thread
+    constexpr int TXP = 8 / PX;                  // patches per block along x (8 points)
+    constexpr int TYP = STP / LPP / TXP;         // patches per block along y
+    constexpr bool X = MASK & HAS_X, PREV = MASK & HAS_PREV, PP = MASK & HAS_PP,
+                   VS = MASK & HAS_VS;
+    constexpr int NBX = 2 * R * PY, NBY = 2 * R * PX, NB = NBX + NBY;
+    constexpr int NOP = (X ? 1 : 0) + (PREV ? 1 : 0) + (PP ? 1 : 0);
+    constexpr int UC = NB;                       // next window plane of each point
+    constexpr int UO = NB + NPT;                 // operands: [op][point]
+    constexpr int NL = NB + NPT * (1 + NOP);
+    const int ch = blockIdx.z;
+    if (!a.chunk_active[ch]) return;
+    extern __shared__ __align__(16) unsigned char st_raw[];
+    Pack<T>* slots = reinterpret_cast<Pack<T>*>(st_raw);      // [DEPTH+1][NL][STP]
+    __shared__ Pack<T> s_sig[LPP], s_insc[LPP], s_a0s[LPP], s_ppc[LPP];
+    if (threadIdx.x < CW) {
+        const int c = ch * CW + threadIdx.x;
+        const int l = threadIdx.x / W, w = threadIdx.x % W;
+        s_sig[l].v[w] = VS ? (T)a.sigma[c] : (T)0;
+        s_insc[l].v[w] = a.p.insc ? (T)a.p.insc[c] : (T)1;
+        s_a0s[l].v[w] = (T)(a.p.a0 * (a.p.xs ? a.p.xs[c] : 1.0));
+        s_ppc[l].v[w] = PP ? (T)a.p.ppc[c] : (T)0;
+    }
+    __syncthreads();
+    const int N = a.op.N;
+    const int lane = threadIdx.x % LPP;
+    const int pt = threadIdx.x / LPP;
+    const int tilesX = (N + TXP * PX - 1) / (TXP * PX);
+    const int x = (blockIdx.x % tilesX) * (TXP * PX) + (pt % TXP) * PX;
+    const int y = (blockIdx.x / tilesX) * (TYP * PY) + (pt / TXP) * PY;
+    if (x >= N || y >= N) return;            // whole patch outside (N % PX == N % PY == 0)
+    const int zb = a.op.zb > 0 ? a.op.zb : ZB;
+    const int z0 = blockIdx.y * zb;
+    const int z1 = min(z0 + zb, N);
+    const int64_t NN = (int64_t)N * N;
+    const Pack<T>* in = reinterpret_cast<const Pack<T>*>(
+        static_cast<const T*>(a.p.in) + ch * a.p.in_cs) + lane;
+    const Pack<T>* xv = X ? reinterpret_cast<const Pack<T>*>(
+        static_cast<const T*>(a.p.x) + ch * a.p.x_cs) + lane : nullptr;
+    const Pack<T>* pv = PREV ? reinterpret_cast<const Pack<T>*>(
+        static_cast<const T*>(a.p.prev) + ch * a.p.prev_cs) + lane : nullptr;
+    const Pack<T>* ppv = PP ? reinterpret_cast<const Pack<T>*>(
+        static_cast<const T*>(a.p.pp) + ch * a.p.pp_cs) + lane : nullptr;
+    Pack<T>* out = reinterpret_cast<Pack<T>*>(static_cast<T*>(a.p.out) + ch * a.p.out_cs) + lane;
+    const T* __restrict__ V = static_cast<const T*>(a.op.V);
+    auto wrap = [&](int v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
+
+    int64_t cxy[NPT];
+#pragma unroll
+    for (int b = 0; b < PY; ++b)
+#pragma unroll
+        for (int q = 0; q < PX; ++q) cxy[b * PX + q] = (x + q) + (int64_t)N * (y + b);
+    // the points around the patch: per row, offsets -R..-1 and PX..PX+R-1 in
+    // x; per column, the same in y (slot d < R: offset d - R, else d - R + P)
+    const int64_t pstep = NN * LPP;
+    const Pack<T>* src_nb[NB];
+#pragma unroll
+    for (int b = 0; b < PY; ++b)
+#pragma unroll
+        for (int d = 0; d < 2 * R; ++d) {
+            const int o = d < R ? d - R : PX + d - R;
+            src_nb[b * 2 * R + d] = in + (wrap(x + o) + (int64_t)N * (y + b) + NN * z0) * LPP;
+        }
+#pragma unroll
+    for (int q = 0; q < PX; ++q)
+#pragma unroll
+        for (int d = 0; d < 2 * R; ++d) {
+            const int o = d < R ? d - R : PY + d - R;
+            src_nb[NBX + q * 2 * R + d] = in + ((x + q) + (int64_t)N * wrap(y + o) + NN * z0) * LPP;
+        }
+    auto slot = [&](int stage, int u) -> Pack<T>* {
+        return slots + ((size_t)stage * NL + u) * STP + threadIdx.x;
+    };
+    auto issue = [&](int zz, int st) {
+        if (zz < z1) {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                cp_async16(slot(st, u), src_nb[u]);
+                src_nb[u] += pstep;
+            }
+            if (zz + 1 < z1) {
+                const int64_t zc = NN * ((zz + 1 + R) % N);
+#pragma unroll
+                for (int q = 0; q < NPT; ++q) cp_async16(slot(st, UC + q), in + (cxy[q] + zc) * LPP);
+            }
+            const int64_t zo = NN * zz;
+            int k = 0;
+            if (X) {
+#pragma unroll
+                for (int q = 0; q < NPT; ++q) cp_async16(slot(st, UO + k * NPT + q), xv + (cxy[q] + zo) * LPP);
+                ++k;
+            }
+            if (PREV) {
+#pragma unroll
+                for (int q = 0; q < NPT; ++q) cp_async16(slot(st, UO + k * NPT + q), pv + (cxy[q] + zo) * LPP);
+                ++k;
+            }
+            if (PP) {
+#pragma unroll
+                for (int q = 0; q < NPT; ++q) cp_async16(slot(st, UO + k * NPT + q), ppv + (cxy[q] + zo) * LPP);
+            }
+        }
+        cp_async_commit();
+    };
+
+    Pack<T> win[2 * R + 1][NPT];
+#pragma unroll
+    for (int o = -R; o <= R; ++o) {
+        const int64_t zq = NN * (((z0 + o) % N + N) % N);
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) win[o + R][q] = ldg_pack(in + (cxy[q] + zq) * LPP);
+    }
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) issue(z0 + d, d);
+
+    const T k1 = (T)a.p.k1;
+    const T c1 = (T)a.op.c1, c2 = (T)a.op.c2;
+    const T dg = (T)(a.p.k1 * a.op.cd + a.p.k0);
+    const T a2 = (T)a.p.a2;
+
+    for (int z = z0; z < z1; ++z) {
+        const int stg = (z - z0) % (DEPTH + 1);
+        issue(z + DEPTH, (z - z0 + DEPTH) % (DEPTH + 1));
+        cp_async_wait<DEPTH>();
+        const int64_t rowz = NN * z;
+        Pack<T> nb[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) nb[u] = *slot(stg, u);
+        const Pack<T> sig = s_sig[lane], insc = s_insc[lane], a0c = s_a0s[lane], ppcc = s_ppc[lane];
+#pragma unroll
+        for (int b = 0; b < PY; ++b) {
+#pragma unroll
+            for (int q = 0; q < PX; ++q) {
+                const int pp_ = b * PX + q;
+                // value of the plane-z point at offset (ox, oy) from point (q, b)
+                auto nbv = [&](int ox, int oy) -> const Pack<T>& {
+                    const int xx = q + ox, yy = b + oy;
+                    if (oy == 0) {
+                        if (xx >= 0 && xx < PX) return win[R][b * PX + xx];
+                        return nb[b * 2 * R + (xx < 0 ? xx + R : R + xx - PX)];
+                    }
+                    if (yy >= 0 && yy < PY) return win[R][yy * PX + q];
+                    return nb[NBX + q * 2 * R + (yy < 0 ? yy + R : R + yy - PY)];
+                };
+                const T vp = VS ? __ldg(V + cxy[pp_] + rowz) : (T)0;
+                Pack<T> res;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    T off = c1 * (nbv(-1, 0).v[w] + nbv(1, 0).v[w] + nbv(0, -1).v[w] +
+                                  nbv(0, 1).v[w] + win[R - 1][pp_].v[w] + win[R + 1][pp_].v[w]);
+                    if (R == 2)
+                        off += c2 * (nbv(-2, 0).v[w] + nbv(2, 0).v[w] + nbv(0, -2).v[w] +
+                                     nbv(0, 2).v[w] + win[0][pp_].v[w] + win[2 * R][pp_].v[w]);
+                    const T stv = k1 * off + (dg + vp - sig.v[w]) * win[R][pp_].v[w];
+                    res.v[w] = insc.v[w] * stv;
+                }
+                int k = 0;
+                if (X) {
+                    const Pack<T> t = *slot(stg, UO + (k++) * NPT + pp_);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) res.v[w] += a0c.v[w] * t.v[w];
+                }
+                if (PREV) {
+                    const Pack<T> t = *slot(stg, UO + (k++) * NPT + pp_);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) res.v[w] -= a2 * t.v[w];
+                }
+                if (PP) {
+                    const Pack<T> t = *slot(stg, UO + (k++) * NPT + pp_);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) res.v[w] -= ppcc.v[w] * t.v[w];
+                }
+                st_pack(out + (cxy[pp_] + rowz) * LPP, res);
+            }
+        }
+        if (z + 1 < z1) {
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) {
+                const Pack<T> nxt = *slot(stg, UC + q);
+#pragma unroll
+                for (int o = 0; o < 2 * R; ++o) win[o][q] = win[o + 1][q];
+                win[2 * R][q] = nxt;
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <typename T, int R, int MASK, int PX, int PY>
+void launch_patch(dim3 grid, cudaStream_t st, const KArgs& a)
+{
+    constexpr int NB = 2 * R * (PX + PY);
+    constexpr int NOP = ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) + ((MASK & HAS_PP) ? 1 : 0);
+    constexpr size_t smem = (size_t)(DEPTH + 1) * (NB + PX * PY * (1 + NOP)) * STP * 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(stencil_patch_kernel<T, R, MASK, PX, PY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    stencil_patch_kernel<T, R, MASK, PX, PY><<<grid, STP, smem, st>>>(a);
+}
+
+template <typename T, int R, int PX, int PY>
+bool launch_patch_masked(int mask, dim3 grid, cudaStream_t st, const KArgs& a)
+{
+    switch (mask) {
+    case 0: launch_patch<T, R, 0, PX, PY>(grid, st, a); break;
+    case HAS_X: launch_patch<T, R, HAS_X, PX, PY>(grid, st, a); break;
+    case HAS_X | HAS_PREV: launch_patch<T, R, HAS_X | HAS_PREV, PX, PY>(grid, st, a); break;
+    case HAS_X | HAS_PP: launch_patch<T, R, HAS_X | HAS_PP, PX, PY>(grid, st, a); break;
+    case HAS_X | HAS_PREV | HAS_PP: launch_patch<T, R, HAS_X | HAS_PREV | HAS_PP, PX, PY>(grid, st, a); break;
+    case HAS_PP: launch_patch<T, R, HAS_PP, PX, PY>(grid, st, a); break;
+    case HAS_VS: launch_patch<T, R, HAS_VS, PX, PY>(grid, st, a); break;
+    case HAS_VS | HAS_PP: launch_patch<T, R, HAS_VS | HAS_PP, PX, PY>(grid, st, a); break;
+    default:
+        return false;
+    }
+    return true;
+}
+
 template <int R, int MASK>
 constexpr int stencil_loads()
 {
@@ -326,6 +564,15 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |
                      (p.useV ? HAS_VS : 0);
     bool ok;
+    if (!jacobi && op.patch == 2 && N % 2 == 0) {
+        // 2 x 2 patches: 8 x (STP / LPP / 4 * 2) points per block
+        constexpr int TYP = STP / LPP / 4;
+        dim3 pg(((N + 7) / 8) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb, r.nchunk);
+        ok = op.order == 2 ? launch_patch_masked<T, 1, 2, 2>(mask, pg, st, a)
+                           : launch_patch_masked<T, 2, 2, 2>(mask, pg, st, a);
+        if (!ok) return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     if (op.order == 2)
         ok = jacobi ? launch_masked<T, 1, true>(mask, grid, st, a)
                     : launch_masked<T, 1, false>(mask, grid, st, a);

@@ -31,6 +31,7 @@ EVC_OPT_CHEB_FORM = 6
 EVC_OPT_BASIS_BF16 = 7
 EVC_OPT_REORTH_ROWS, EVC_OPT_STENCIL_ZB, EVC_OPT_CSR_THREADS = 8, 9, 10
 EVC_OPT_METHOD = 11
+EVC_OPT_STENCIL_PATCH = 12
 EVC_METHOD_LANCZOS, EVC_METHOD_ARNOLDI = 0, 1
 EVC_CHEB_FACTORED, EVC_CHEB_CLENSHAW = 0, 1
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1
@@ -67,7 +68,8 @@ class evc_prof_rec(C.Structure):
 
 
 class evc_tuning(C.Structure):
-    _fields_ = [("stencil_zb", C.c_int), ("csr_threads", C.c_int), ("reorth_rows", C.c_int),
+    _fields_ = [("stencil_zb", C.c_int), ("stencil_patch", C.c_int), ("csr_threads", C.c_int),
+                ("reorth_rows", C.c_int),
                 ("steps", C.c_int), ("ms_before", C.c_double), ("ms_after", C.c_double)]
 
 

@@ -67,6 +67,7 @@ def test_autotune_choices_and_parity():
     with ctx:
         t = ctx.autotune(len(shifts), m, k)
         assert t["stencil_zb"] in (16, 30) and t["csr_threads"] == 0
+        assert t["stencil_patch"] in (1, 2)
         assert t["reorth_rows"] in (1728, 3456, 6912, 13824)
         assert t["ms_before"] > 0 and t["ms_after"] > 0 and t["steps"] == 6
         q = ctx.count_slices(shifts, m, k)[1]
@@ -96,3 +97,37 @@ def test_tuning_options_validate():
                 ctx.set_option(opt, bad)
         with pytest.raises(evc.EvcError):
             ctx.autotune(0, 8, 4)
+
+
+@pytest.mark.parametrize("N,order", [(10, 2), (16, 4), (12, 2), (9, 2)])
+@pytest.mark.parametrize("prec", [evc.EVC_FP64, evc.EVC_MIXED])
+def test_stencil_patch_agrees_with_single_points(N, order, prec):
+    # 2 x 2 patches (odd N falls back to one point per thread)
+    V = I.gaussian_wells(N, 0.3, nwells=4, seed=1)
+    shifts, m, k = [-2.0, 0.5], 40, 10
+    res = []
+    for patch in (1, 2):
+        with evc.Context.stencil(N, 0.3, order, V, precision=prec) as ctx:
+            ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, 8, 1.0)
+            ctx.set_option(evc.EVC_OPT_STENCIL_PATCH, patch)
+            res.append(ctx.count_slices(shifts, m, k, seed=0))
+    if prec == evc.EVC_FP64:
+        assert np.max(np.abs(res[0][1] - res[1][1])) < 1e-10
+        P = O.Problem.stencil(N, 0.3, order, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
+        qr, _, _ = O.count(P, shifts, m, k, seed=0)
+        assert np.max(np.abs(res[1][1] - qr)) < 1e-8
+    else:
+        assert np.max(np.abs(res[0][0] - res[1][0])) < 0.05
+
+
+def test_stencil_patch_unpreconditioned_and_zb():
+    # the shifted-Hamiltonian pass with -beta q_(i-1) (operand sets V and V+pp)
+    V = I.gaussian_wells(14, 0.3, nwells=4, seed=1)
+    P = O.Problem.stencil(14, 0.3, 2, V, O.PREC_NONE)
+    qr, _, _ = O.count(P, [-1.0, 0.7], 33, 12, seed=0)
+    with evc.Context.stencil(14, 0.3, 2, V, precision=evc.EVC_FP64) as ctx:
+        ctx.set_option(evc.EVC_OPT_STENCIL_PATCH, 2)
+        for zb in (3, 32):
+            ctx.set_option(evc.EVC_OPT_STENCIL_ZB, zb)
+            q = ctx.count_slices([-1.0, 0.7], 33, 12, seed=0)[1]
+            assert np.max(np.abs(q - qr)) < 1e-8
