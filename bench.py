@@ -114,7 +114,7 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
     return ctx
 
 
-def _roofline(evc, recs, peak, peak_kind):
+def _roofline(evc, recs, peak, peak_kind, stencil_name="stencil_pass_kernel"):
     """Roofline of the kernel class with the largest device time in the launch
     list: achieved = sum of its launches' algorithmic bytes / sum of their
     CUDA-event durations."""
@@ -133,7 +133,7 @@ def _roofline(evc, recs, peak, peak_kind):
     if best is None:
         return None, per_kind
     name, t, b, cnt = best
-    kernel = {"stencil": "stencil_pass_kernel", "csr": "csr_pass_kernel",
+    kernel = {"stencil": stencil_name, "csr": "csr_pass_kernel",
               "dots": "reorth_dots_kernel", "update": "reorth_update_kernel"}.get(name, name)
     ach = b / (t * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": kernel, "achieved": round(ach, 1), "peak": peak,
@@ -150,7 +150,8 @@ def _attach_traffic(roof):
     """DRAM traffic of one launch of the dominant kernel from the committed ncu
     capture, only while the kernel's source is unchanged since the capture."""
     import hashlib
-    rec = {"stencil_pass_kernel": "profiles/stencil_pass_fd64_traffic.json"}.get(roof["kernel"])
+    rec = {"stencil_pass_kernel": "profiles/stencil_pass_fd64_traffic.json",
+           "stencil_patch_kernel": "profiles/stencil_patch_fd64_traffic.json"}.get(roof["kernel"])
     if not rec or not os.path.exists(os.path.join(ROOT, rec)):
         return
     d = json.load(open(os.path.join(ROOT, rec)))
@@ -227,7 +228,13 @@ def run_ours(args):
     timed(ctx, 1, 0, profile=True)
     recs = evc.evc_get_profile(ctx.h)
     launches_per_step = len(recs)
-    roof, per_kind = _roofline(evc, recs, peak, peak_kind)
+    # the stencil class runs the patch kernel when the tuner chose 2 x 2 patches
+    # (passes without Jacobi scaling, N even)
+    sname = "stencil_pass_kernel"
+    if W.kind == "stencil" and tuning and tuning.get("stencil_patch") == 2 \
+            and W.precond != "jacobi" and W.N % 2 == 0:
+        sname = "stencil_patch_kernel"
+    roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname)
     # ---- e2e: host V (pinned) -> device, count, per-probe results -> host
     Vh = torch.from_numpy(W.potential().astype(np.float32)).pin_memory() if W.kind == "stencil" else None
     evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
