@@ -95,6 +95,7 @@ class ClockSampler:
 
 _CHEB_FORM = [0]     # EVC_CHEB_FACTORED; --cheb-form clenshaw sets 1
 _METHOD = [0]        # EVC_METHOD_LANCZOS; --method arnoldi sets 1
+_SHAPES = {"patch": 0, "zb": 0}   # 0: library default
 
 
 def _make_ctx(evc, W, precision, stream_ptr, V=None):
@@ -110,6 +111,12 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
     if W.precond == "cheb":
         evc.evc_set_option(ctx.h, evc.EVC_OPT_CHEB_FORM, _CHEB_FORM[0])
     evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, _METHOD[0])
+    if W.kind == "stencil":
+        # fixed tile shapes (the autotuner, when it runs, starts from these)
+        if _SHAPES["patch"]:
+            evc.evc_set_option(ctx.h, evc.EVC_OPT_STENCIL_PATCH, _SHAPES["patch"])
+        if _SHAPES["zb"]:
+            evc.evc_set_option(ctx.h, evc.EVC_OPT_STENCIL_ZB, _SHAPES["zb"])
     ctx.reserve(len(W.shifts), W.nprobe, W.maxsteps)
     return ctx
 
@@ -231,8 +238,8 @@ def run_ours(args):
     # the stencil class runs the patch kernel when the tuner chose 2 x 2 patches
     # (passes without Jacobi scaling, N even)
     sname = "stencil_pass_kernel"
-    if W.kind == "stencil" and tuning and tuning.get("stencil_patch") == 2 \
-            and W.precond != "jacobi" and W.N % 2 == 0:
+    patch = tuning.get("stencil_patch") if tuning else _SHAPES["patch"]
+    if W.kind == "stencil" and patch == 2 and W.precond != "jacobi" and W.N % 2 == 0:
         sname = "stencil_patch_kernel"
     roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname)
     # ---- e2e: host V (pinned) -> device, count, per-probe results -> host
@@ -508,6 +515,10 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg")
     ap.add_argument("--skip-bf16", action="store_true", help="omit the BF16-basis accuracy trial")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
+    ap.add_argument("--stencil-patch", type=int, default=0, choices=[0, 1, 2],
+                    help="points per thread of the stencil pass (with --no-autotune)")
+    ap.add_argument("--stencil-zb", type=int, default=0,
+                    help="z planes per block of the stencil pass (with --no-autotune)")
     ap.add_argument("--method", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="estimator: preconditioned Lanczos (default) or the Arnoldi-type variant")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
@@ -518,6 +529,7 @@ def main():
     args = ap.parse_args()
     _CHEB_FORM[0] = 0 if args.cheb_form == "factored" else 1
     _METHOD[0] = 0 if args.method == "lanczos" else 1
+    _SHAPES["patch"], _SHAPES["zb"] = args.stencil_patch, args.stencil_zb
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":
