@@ -271,16 +271,32 @@ stencil_pass_kernel(KArgs a)
 // output of the 7-point stencil from 4R + 1 to R(PX + PY)/2 + 1 plus the
 // pointwise operands.  Per-point arithmetic and summation order are those of
 // stencil_pass_kernel.  N must be a multiple of PX and PY.
-constexpr int STP = 64;    // threads per block of the patch variant
+constexpr int STP = 128;   // threads per block of the patch variant
+constexpr int DMAXP = 3;   // planes of loads in flight, patch variant (at most)
+constexpr int PTW = 8;     // patch-variant block tile width (points along x)
+
+// Planes in flight of one patch-kernel instance: DMAXP, or fewer when its
+// slots (NL per plane per thread) would not fit 220 KB of shared memory.
+template <int R, int MASK, int PX, int PY>
+__host__ __device__ constexpr int patch_depth()
+{
+    constexpr int nl = 2 * R * (PX + PY) +
+                       PX * PY * (1 + ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) +
+                                  ((MASK & HAS_PP) ? 1 : 0));
+    constexpr int fit = 220 * 1024 / (nl * STP * 16) - 1;
+    return fit < DMAXP ? fit : DMAXP;
+}
 
 template <typename T, int R, int MASK, int PX, int PY>
 __global__ void __launch_bounds__(STP)
 stencil_patch_kernel(KArgs a)
 {
+    constexpr int DEPTHP = patch_depth<R, MASK, PX, PY>();
+    static_assert(DEPTHP >= 1, "patch kernel slots do not fit shared memory");
     constexpr int W = 16 / sizeof(T);
     constexpr int LPP = CW / W;
     constexpr int NPT = PX * PY;                 // points per thread
-    constexpr int TXP = 8 / PX;                  // patches per block along x (8 points)
+    constexpr int TXP = PTW / PX;                // patches per block along x
     constexpr int TYP = STP / LPP / TXP;         // patches per block along y
     constexpr bool X = MASK & HAS_X, PREV = MASK & HAS_PREV, PP = MASK & HAS_PP,
                    VS = MASK & HAS_VS;
@@ -292,7 +308,7 @@ stencil_patch_kernel(KArgs a)
     const int ch = blockIdx.z;
     if (!a.chunk_active[ch]) return;
     extern __shared__ __align__(16) unsigned char st_raw[];
-    Pack<T>* slots = reinterpret_cast<Pack<T>*>(st_raw);      // [DEPTH+1][NL][STP]
+    Pack<T>* slots = reinterpret_cast<Pack<T>*>(st_raw);      // [DEPTHP+1][NL][STP]
     __shared__ Pack<T> s_sig[LPP], s_insc[LPP], s_a0s[LPP], s_ppc[LPP];
     if (threadIdx.x < CW) {
         const int c = ch * CW + threadIdx.x;
@@ -392,7 +408,7 @@ stencil_patch_kernel(KArgs a)
         for (int q = 0; q < NPT; ++q) win[o + R][q] = ldg_pack(in + (cxy[q] + zq) * LPP);
     }
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) issue(z0 + d, d);
+    for (int d = 0; d < DEPTHP; ++d) issue(z0 + d, d);
 
     const T k1 = (T)a.p.k1;
     const T c1 = (T)a.op.c1, c2 = (T)a.op.c2;
@@ -400,9 +416,9 @@ stencil_patch_kernel(KArgs a)
     const T a2 = (T)a.p.a2;
 
     for (int z = z0; z < z1; ++z) {
-        const int stg = (z - z0) % (DEPTH + 1);
-        issue(z + DEPTH, (z - z0 + DEPTH) % (DEPTH + 1));
-        cp_async_wait<DEPTH>();
+        const int stg = (z - z0) % (DEPTHP + 1);
+        issue(z + DEPTHP, (z - z0 + DEPTHP) % (DEPTHP + 1));
+        cp_async_wait<DEPTHP>();
         const int64_t rowz = NN * z;
         Pack<T> nb[NB];
 #pragma unroll
@@ -472,7 +488,8 @@ void launch_patch(dim3 grid, cudaStream_t st, const KArgs& a)
 {
     constexpr int NB = 2 * R * (PX + PY);
     constexpr int NOP = ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) + ((MASK & HAS_PP) ? 1 : 0);
-    constexpr size_t smem = (size_t)(DEPTH + 1) * (NB + PX * PY * (1 + NOP)) * STP * 16;
+    constexpr size_t smem =
+        (size_t)(patch_depth<R, MASK, PX, PY>() + 1) * (NB + PX * PY * (1 + NOP)) * STP * 16;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(stencil_patch_kernel<T, R, MASK, PX, PY>,
@@ -565,9 +582,10 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
                      (p.useV ? HAS_VS : 0);
     bool ok;
     if (!jacobi && op.patch == 2 && N % 2 == 0) {
-        // 2 x 2 patches: 8 x (STP / LPP / 4 * 2) points per block
-        constexpr int TYP = STP / LPP / 4;
-        dim3 pg(((N + 7) / 8) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb, r.nchunk);
+        // 2 x 2 patches: PTW x (2 TYP) points per block
+        constexpr int TYP = STP / LPP / (PTW / 2);
+        dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb,
+                r.nchunk);
         ok = op.order == 2 ? launch_patch_masked<T, 1, 2, 2>(mask, pg, st, a)
                            : launch_patch_masked<T, 2, 2, 2>(mask, pg, st, a);
         if (!ok) return cudaErrorInvalidValue;

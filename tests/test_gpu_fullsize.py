@@ -33,7 +33,7 @@ def _lib():
     evc.load()
 
 
-def _gpu(W, precision):
+def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS):
     import torch
     if W.kind == "stencil":
         ctx = evc.Context.stencil(W.N, W.h, W.order, W.potential(), precision=precision)
@@ -48,6 +48,7 @@ def _gpu(W, precision):
             pytest.skip(f"workspace {need / 1e9:.0f} GB does not fit")
         ctx.set_precond(kind, *W.prec_params)
         evc.evc_set_option(ctx.h, evc.EVC_OPT_MIN_STEPS, W.min_steps)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, method)
         out = ctx.count_slices(W.shifts, W.nprobe, W.maxsteps, tol=W.tol, seed=0)
     torch.cuda.empty_cache()
     return out
@@ -118,3 +119,20 @@ def test_slicing_96_fullsize():
         assert np.max(np.abs(qmx[s, ids] - ref[s])) < MIXED_TOL
     # slice counts are differences of n_below; n_below is non-decreasing up to noise
     assert np.all(np.diff(Lmx) > -2.0)
+
+
+def test_fd_hamiltonian_64_arnoldi_fullsize():
+    # the Arnoldi-type estimator (Sec. 4) on the benchmark workload: FP64 and
+    # mixed GPU counts against the numpy Arnoldi oracle on two sampled probes
+    from oracle import arnoldi as AR
+    W = workloads.fd_hamiltonian_64()
+    L64, q64, _ = _gpu(W, evc.EVC_FP64, evc.EVC_METHOD_ARNOLDI)
+    Lmx, qmx, _ = _gpu(W, evc.EVC_MIXED, evc.EVC_METHOD_ARNOLDI)
+    P = _oracle_problem(W)
+    pids = [5, 41]
+    for s in range(len(W.shifts)):
+        qr, _, _ = AR.count(P, [W.shifts[s]], len(pids), W.maxsteps, seed=0, probe_ids=pids)
+        for j, pid in enumerate(pids):
+            assert abs(q64[s, pid] - qr[0, j]) < FP64_TOL
+            assert abs(qmx[s, pid] - qr[0, j]) < MIXED_TOL
+    assert abs((Lmx[-1] - Lmx[0]) - (L64[-1] - L64[0])) < MIXED_TOL
