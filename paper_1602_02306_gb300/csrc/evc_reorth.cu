@@ -147,12 +147,17 @@ __device__ __forceinline__ void row_range(int64_t n, int nblk, int blk, int64_t&
 // stages, so the bytes in flight are set by shared memory, not registers;
 // eight consumer warps compute from shared memory and release the stages.
 constexpr int CWARPS = 8;                       // consumer warps
-constexpr int BTHREADS = (CWARPS + 1) * 32;     // + one producer warp
 constexpr int DSTAGE = 4096;                    // bytes per stage, dot kernel
 constexpr int NSW = 2;                          // stages per consumer warp, dot kernel
+constexpr int NPROD = 2;                        // producer warps, dot kernel
+constexpr int DTHREADS = (CWARPS + NPROD) * 32; // threads of the dot kernel
+static_assert(CWARPS % NPROD == 0, "a consumer warp's ring must have one producer");
 constexpr int DNS = CWARPS * NSW;               // stages, dot kernel
 constexpr int USTAGE = 8192;                    // bytes per stage, update kernel
 constexpr int UNS = 10;                         // stages, update kernel
+constexpr int UWARPS = CWARPS + NPROD;          // warps of the update kernel
+constexpr int UTHREADS = UWARPS * 32;           // threads of the update kernel
+static_assert(UNS % NPROD == 0, "a stage of the update ring must have one producer");
 
 // part_dot[ch][blk][j][lane]  = sum_{rows of blk} P_j[row][lane] * w[row][lane]
 // part_gram[ch][blk][j][lane] = sum_{rows of blk} P_j[row][lane] * P_{i-1}[row][lane]
@@ -164,7 +169,7 @@ constexpr int UNS = 10;                         // stages, update kernel
 // waits for is always one phase ahead of the previous item in that stage,
 // which the same warp consumed (mbarrier parities cannot alias).
 template <typename T>
-__global__ void __launch_bounds__(BTHREADS)
+__global__ void __launch_bounds__(DTHREADS, 2)
 reorth_dots_kernel(Run r, int i)
 {
     constexpr int TR = DSTAGE / (CW * (int)sizeof(T));   // rows per tile
@@ -204,7 +209,13 @@ reorth_dots_kernel(Run r, int i)
     __syncthreads();
     typedef typename Acc<T>::run RTy;
     bool ok = true;
-    if (warp == CWARPS) {
+    if (warp >= CWARPS) {
+        // Producer p issues the items j = p, p + NPROD, ... -- the rings of the
+        // consumer warps cw = j % CWARPS with cw % NPROD == p, each ring in
+        // order -- so that NPROD threads issue bulk copies (one thread issues
+        // about one copy per quarter microsecond); producer 0 also issues the
+        // w and q_i tiles.
+        const int pw = warp - CWARPS;
         if (lane == 0) {
             int64_t lastk[DNS];                  // last item issued into each stage
             int lastt[2] = {-1, -1};             // last tile issued into each w/q buffer
@@ -213,14 +224,16 @@ reorth_dots_kernel(Run r, int i)
                 const int64_t row0 = r0 + (int64_t)t * TR;
                 const uint32_t bytes = (uint32_t)(min((int64_t)TR, r1 - row0) * CW * sizeof(T));
                 const int b = t & 1;
-                if (t >= 2 && !(ok = mbar_wait(&wqempty[b], ((t >> 1) - 1) & 1))) break;
-                lastt[b] = t;
-                mbar_arrive_expect_tx(&wqfull[b], 2 * bytes);
-                ok = checked_bulk(wq + (size_t)(2 * b) * TR * CW, w + row0 * CW, bytes, &wqfull[b],
-                                  lo, hi, r.err) &&
-                     checked_bulk(wq + (size_t)(2 * b + 1) * TR * CW, q + row0 * CW, bytes,
-                                  &wqfull[b], lo, hi, r.err);
-                for (int j = 0; j < i && ok; ++j) {
+                if (pw == 0) {
+                    if (t >= 2 && !(ok = mbar_wait(&wqempty[b], ((t >> 1) - 1) & 1))) break;
+                    lastt[b] = t;
+                    mbar_arrive_expect_tx(&wqfull[b], 2 * bytes);
+                    ok = checked_bulk(wq + (size_t)(2 * b) * TR * CW, w + row0 * CW, bytes,
+                                      &wqfull[b], lo, hi, r.err) &&
+                         checked_bulk(wq + (size_t)(2 * b + 1) * TR * CW, q + row0 * CW, bytes,
+                                      &wqfull[b], lo, hi, r.err);
+                }
+                for (int j = pw; j < i && ok; j += NPROD) {
                     // k-th item of consumer warp cw lives in stage cw*NSW + k % NSW
                     const int cw = j % CWARPS;
                     const int64_t k = (int64_t)t * ((i - cw + CWARPS - 1) / CWARPS) + j / CWARPS;
@@ -356,7 +369,7 @@ __global__ void reorth_coef_kernel(Run r, int i)
 // consumer warp q owns rows q*RPW.. of the tile in registers and applies
 // every P_j stage to them, then writes the tile back.
 template <typename T>
-__global__ void __launch_bounds__(BTHREADS)
+__global__ void __launch_bounds__(UTHREADS, 2)
 reorth_update_kernel(Run r, int i)
 {
     constexpr int TR = USTAGE / (CW * (int)sizeof(T));   // rows per tile
@@ -372,7 +385,7 @@ reorth_update_kernel(Run r, int i)
     uint64_t* empty = full + UNS;
     uint64_t* wfull = empty + UNS;
     uint64_t* wempty = wfull + 2;
-    __shared__ double red[CWARPS + 1][CW];
+    __shared__ double red[UWARPS][CW];
     __shared__ int s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < i * CW; e += blockDim.x)
@@ -400,7 +413,11 @@ reorth_update_kernel(Run r, int i)
     typedef typename Acc<T>::run RTy;
     bool ok = true;
     double acc = 0.0;
-    if (warp == CWARPS) {
+    if (warp >= CWARPS) {
+        // Producer p issues the items with index = p (mod NPROD) -- the stages
+        // s = p (mod NPROD), each in order -- so that NPROD threads issue bulk
+        // copies; producer 0 also issues the w tiles.
+        const int pw = warp - CWARPS;
         if (lane == 0) {
             int64_t item = 0;
             int64_t lastk[UNS];
@@ -410,12 +427,15 @@ reorth_update_kernel(Run r, int i)
                 const int64_t row0 = r0 + (int64_t)t * TR;
                 const uint32_t bytes = (uint32_t)(min((int64_t)TR, r1 - row0) * CW * sizeof(T));
                 const int b = t & 1;
-                if (t >= 2 && !(ok = mbar_wait(&wempty[b], ((t >> 1) - 1) & 1))) break;
-                lastt[b] = t;
-                mbar_arrive_expect_tx(&wfull[b], bytes);
-                ok = checked_bulk(wbuf + (size_t)b * TR * CW, w + row0 * CW, bytes, &wfull[b], lo, hi,
-                                  r.err);
+                if (pw == 0) {
+                    if (t >= 2 && !(ok = mbar_wait(&wempty[b], ((t >> 1) - 1) & 1))) break;
+                    lastt[b] = t;
+                    mbar_arrive_expect_tx(&wfull[b], bytes);
+                    ok = checked_bulk(wbuf + (size_t)b * TR * CW, w + row0 * CW, bytes, &wfull[b],
+                                      lo, hi, r.err);
+                }
                 for (int j = 0; j < i && ok; ++j, ++item) {
+                    if ((int)(item % NPROD) != pw) continue;
                     const int s = (int)(item % UNS);
                     if (item >= UNS && !(ok = mbar_wait(&empty[s], ((item / UNS) - 1) & 1))) break;
                     lastk[s] = item;
@@ -500,7 +520,7 @@ reorth_update_kernel(Run r, int i)
     __threadfence();
     {
         double ps = 0.0;
-        for (int b = warp; b < r.nblk; b += CWARPS + 1)
+        for (int b = warp; b < r.nblk; b += UWARPS)
             ps += r.part_nrm[((int64_t)ch * r.nblk + b) * CW + lane];
         red[warp][lane] = ps;
     }
@@ -510,7 +530,7 @@ reorth_update_kernel(Run r, int i)
         if (r.kdone[c] == 0) {
             double nrm2 = 0.0;
 #pragma unroll
-            for (int q = 0; q < CWARPS + 1; ++q) nrm2 += red[q][ln];
+            for (int q = 0; q < UWARPS; ++q) nrm2 += red[q][ln];
             const double beta = sqrt(nrm2);
             const double al = r.alpha[(int64_t)(i - 1) * r.ncol + c];
             const double bprev = r.beta[(int64_t)(i - 1) * r.ncol + c];
@@ -686,7 +706,7 @@ cudaError_t launch_dots(const Run& r, int i, cudaStream_t st)
                              (int)dots_smem<T>(kMaxSteps));
         attr_set = true;
     }
-    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), BTHREADS, dots_smem<T>(i), st>>>(r, i);
+    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), DTHREADS, dots_smem<T>(i), st>>>(r, i);
     return cudaGetLastError();
 }
 
@@ -712,7 +732,7 @@ cudaError_t launch_update(const Run& r, int i, cudaStream_t st)
                              (int)update_smem<T>(kMaxSteps));
         attr_set = true;
     }
-    reorth_update_kernel<T><<<dim3(r.nblk, r.nchunk), BTHREADS, update_smem<T>(i), st>>>(r, i);
+    reorth_update_kernel<T><<<dim3(r.nblk, r.nchunk), UTHREADS, update_smem<T>(i), st>>>(r, i);
     return cudaGetLastError();
 }
 
