@@ -215,7 +215,8 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       itself stays FP32, so this measures the accuracy of
  *                       BF16 storage, not its bandwidth.  Default 0.
  *   EVC_OPT_REORTH_ROWS: rows per block of the reorthogonalisation kernels
- *                       (default 3456, at least 1728).  It sets the summation
+ *                       (default 3456; at least 64, and at most max(ceil(n/1728),
+ *                       min(ceil(n/64), 512)) blocks per chunk).  It sets the summation
  *                       order of the dot products, so results may change in the
  *                       last bits; it never depends on how many columns a call
  *                       batches, so a column's result is the same alone or in
@@ -294,8 +295,8 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB) times
  *                  points per thread 1 / 2x2 (EVC_OPT_STENCIL_PATCH),
  *   CSR pass:      threads per block 128 / 256 / 512 (EVC_OPT_CSR_THREADS),
- *   reorthogonalisation: rows per block 1728 / 3456 / 6912 / 13824
- *                  (EVC_OPT_REORTH_ROWS),
+ *   reorthogonalisation: rows per block 64 ... 13824 within the allowed
+ *                  block counts (EVC_OPT_REORTH_ROWS),
  * tuning the operator pass first.  The choice stays in the context for later
  * calls (and contexts cloned from it); `out` (may be NULL) reports it with the
  * device time of one short count before and after.  Needs the workspace of a

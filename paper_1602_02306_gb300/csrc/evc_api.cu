@@ -159,7 +159,7 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     const int nchunk = (ncol_real + CW - 1) / CW;
     const int ncol = nchunk * CW;
     const int nblk = choose_nblk(c->n, c->reorth_rows);
-    const int nblk_max = choose_nblk(c->n, kMinReorthRows);   // any tuned value fits
+    const int nblk_max = reorth_max_blocks(c->n);   // any allowed value fits
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -1406,6 +1406,9 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
     if (option == EVC_OPT_REORTH_ROWS) {
         if (value < kMinReorthRows || value > ((int64_t)1 << 30))
             return fail(ctx, EVC_EINVAL, "reorthogonalisation rows per block must be >= %d", kMinReorthRows);
+        if (choose_nblk(ctx->n, (int)value) > reorth_max_blocks(ctx->n))
+            return fail(ctx, EVC_EINVAL, "at most %d reorthogonalisation blocks per chunk for n = %lld",
+                        reorth_max_blocks(ctx->n), (long long)ctx->n);
         ctx->reorth_rows = (int)value;
         ++ctx->prec_version;
         drop_graph(ctx);
@@ -1582,9 +1585,9 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
         double best = 1e300;
         int br = 3456;
         int last_nblk = -1;
-        for (int rows : {1728, 3456, 6912, 13824}) {
+        for (int rows : {64, 128, 256, 512, 1024, 1728, 3456, 6912, 13824}) {
             const int nb = choose_nblk(ctx->n, rows);
-            if (nb == last_nblk) continue;
+            if (nb == last_nblk || nb > reorth_max_blocks(ctx->n)) continue;
             last_nblk = nb;
             ctx->reorth_rows = rows;
             double t;

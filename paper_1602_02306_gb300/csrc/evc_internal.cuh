@@ -116,9 +116,18 @@ struct CsrOp {
     int threads;            // threads per block: 128, 256 (default) or 512 (tuned)
 };
 
-// Smallest rows-per-block of the reorthogonalisation kernels that a tuned
-// context may use; the workspace sizes the per-block partial sums for it.
-constexpr int kMinReorthRows = 1728;
+// Rows per block of the reorthogonalisation kernels that a tuned context may
+// use: at least kMinReorthRows, and no more blocks per chunk than
+// reorth_max_blocks(n) (the workspace sizes the per-block partial sums for
+// that many) -- small problems may split into up to 512 blocks, large ones
+// down to 1728 rows per block.
+constexpr int kMinReorthRows = 64;
+inline int reorth_max_blocks(int64_t n)
+{
+    const int64_t big = (n + 1727) / 1728, small = (n + kMinReorthRows - 1) / kMinReorthRows;
+    const int64_t m = big > (small < 512 ? small : 512) ? big : (small < 512 ? small : 512);
+    return (int)(m < 65535 ? (m > 0 ? m : 1) : 65535);
+}
 
 // Kernel launchers (T = float for EVC_MIXED, double for EVC_FP64).
 template <typename T>

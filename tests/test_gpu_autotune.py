@@ -55,7 +55,7 @@ def test_reorth_rows_reorder_sums_only():
     P = O.Problem.stencil(25, 0.3, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
     qr, _, _ = O.count(P, shifts, m, k, seed=0)
     with ctx:
-        for rows in (1728, 3456, 6912, 100000):
+        for rows in (64, 1728, 3456, 6912, 100000):
             ctx.set_option(evc.EVC_OPT_REORTH_ROWS, rows)
             q = ctx.count_slices(shifts, m, k)[1]
             assert np.max(np.abs(q - qr)) < 1e-8
@@ -68,7 +68,7 @@ def test_autotune_choices_and_parity():
         t = ctx.autotune(len(shifts), m, k)
         assert t["stencil_zb"] in (16, 30) and t["csr_threads"] == 0
         assert t["stencil_patch"] in (1, 2)
-        assert t["reorth_rows"] in (1728, 3456, 6912, 13824)
+        assert t["reorth_rows"] in (64, 128, 256, 512, 1024, 1728, 3456, 6912, 13824)
         assert t["ms_before"] > 0 and t["ms_after"] > 0 and t["steps"] == 6
         q = ctx.count_slices(shifts, m, k)[1]
     P = O.Problem.stencil(30, 0.3, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
@@ -91,7 +91,7 @@ def test_autotune_csr_and_batch_independence():
 def test_tuning_options_validate():
     V, ctx = _stencil_ctx(8)
     with ctx:
-        for opt, bad in ((evc.EVC_OPT_REORTH_ROWS, 1000), (evc.EVC_OPT_STENCIL_ZB, -1),
+        for opt, bad in ((evc.EVC_OPT_REORTH_ROWS, 32), (evc.EVC_OPT_STENCIL_ZB, -1),
                          (evc.EVC_OPT_CSR_THREADS, 256)):
             with pytest.raises(evc.EvcError):
                 ctx.set_option(opt, bad)
@@ -131,3 +131,22 @@ def test_stencil_patch_unpreconditioned_and_zb():
             ctx.set_option(evc.EVC_OPT_STENCIL_ZB, zb)
             q = ctx.count_slices([-1.0, 0.7], 33, 12, seed=0)[1]
             assert np.max(np.abs(q - qr)) < 1e-8
+
+
+def test_small_problem_splits_rows():
+    # n = 1024: the tuner may split the reorthogonalisation into 64-row blocks;
+    # FP64 results stay on the oracle
+    csr = I.laplace2d_dirichlet(32)
+    P = O.Problem.csr_matrix(csr, O.PREC_JACOBI, jac_eps=1e-3)
+    qr, _, _ = O.count(P, [1.0, 2.0], 16, 40, seed=0)
+    with evc.Context.csr(csr, precision=evc.EVC_FP64) as ctx:
+        ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        for rows in (64, 256):
+            ctx.set_option(evc.EVC_OPT_REORTH_ROWS, rows)
+            q = ctx.count_slices([1.0, 2.0], 16, 40, seed=0)[1]
+            assert np.max(np.abs(q - qr)) < 1e-8
+        t = ctx.autotune(2, 16, 40)
+        q = ctx.count_slices([1.0, 2.0], 16, 40, seed=0)[1]
+        assert np.max(np.abs(q - qr)) < 1e-8
+        with pytest.raises(evc.EvcError):
+            ctx.set_option(evc.EVC_OPT_REORTH_ROWS, 1)
