@@ -48,24 +48,25 @@ class Workload:
 
 # Lowest eigenvalue of H = -1/2 Lap_h + V on the periodic 64^3 grid (7-point,
 # h = 0.3, 32 wells, well seed 1) by scipy.sparse.linalg.eigsh (ARPACK,
-# which='SA', tol 1e-10), and the 300th/301st eigenvalues by shift-invert
-# eigsh around lambda_min - 0.5 (320 eigenvalues, tol 1e-10).
+# which='SA', tol 1e-10).
 FD64_LAMBDA_MIN = -3.2826731738772574
-FD64_LAMBDA_300 = None
-FD64_LAMBDA_301 = None
+
+# Upper endpoint with exactly 300 eigenvalues below it: n_-(H - eta I) = 300 by
+# Sylvester's law of inertia, counting the negative pivots of a symmetric-mode
+# sparse LU of H - eta I (shift_search.py, k-section of [0.2, 1.6]: 0.48 -> 284,
+# 0.4912 -> 289, 0.5024 -> 294, 0.5136 -> 300, 0.536 -> 309 eigenvalues below).
+FD64_ETA = 0.5136
 
 
 def fd64_eta() -> float:
-    if FD64_LAMBDA_300 is None:
-        return FD64_LAMBDA_MIN + 2.0
-    return 0.5 * (FD64_LAMBDA_300 + FD64_LAMBDA_301)
+    return FD64_ETA
 
 
 def fd_hamiltonian_64() -> Workload:
     """3D FD Hamiltonian, 7-point periodic 64^3 (n = 262,144), h = 0.3, 32
-    Gaussian wells; [lambda_min - 1, eta], eta between the 300th and 301st
-    eigenvalues; Chebyshev degree-8 kinetic preconditioner (c = 1); 64
-    probes (seed 0); 30 Lanczos steps."""
+    Gaussian wells; [lambda_min - 1, eta] with exactly 300 eigenvalues in it
+    (eta between the 300th and 301st); Chebyshev degree-8 kinetic
+    preconditioner (c = 1); 64 probes (seed 0); 30 Lanczos steps."""
     return Workload(name="fd_hamiltonian_64^3_7pt_cheb8_m64_k30", kind="stencil",
                     shifts=[FD64_LAMBDA_MIN - 1.0, fd64_eta()], nprobe=64, maxsteps=30,
                     precond="cheb", prec_params=(8, 1.0), N=64, h=0.3, order=2)

@@ -136,3 +136,19 @@ def test_fd_hamiltonian_64_arnoldi_fullsize():
             assert abs(q64[s, pid] - qr[0, j]) < FP64_TOL
             assert abs(qmx[s, pid] - qr[0, j]) < MIXED_TOL
     assert abs((Lmx[-1] - Lmx[0]) - (L64[-1] - L64[0])) < MIXED_TOL
+
+
+def test_fd_hamiltonian_64_exact_count_statistical():
+    # [lambda_min - 1, eta] holds exactly 300 eigenvalues (Sylvester inertia,
+    # workloads.FD64_ETA).  At 50 steps both estimators are within 4 sample
+    # standard errors of it (at the workload's 30 steps the quadrature is not
+    # yet converged: ~249).
+    W = workloads.fd_hamiltonian_64()
+    for method in (evc.EVC_METHOD_LANCZOS, evc.EVC_METHOD_ARNOLDI):
+        with evc.Context.stencil(W.N, W.h, W.order, W.potential(), precision=evc.EVC_MIXED) as ctx:
+            ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, *W.prec_params)
+            ctx.set_option(evc.EVC_OPT_METHOD, method)
+            L, q, st = ctx.count_slices(W.shifts, W.nprobe, 50, seed=0)
+        d = q[1] - q[0]
+        se = d.std(ddof=1) / np.sqrt(d.size)
+        assert abs((L[1] - L[0]) - 300.0) < 4.0 * se
