@@ -418,6 +418,21 @@ int evc_gauss_quadrature_static(const double* d_alpha, const double* d_beta, con
                                 int k, int ncol, double vnorm2, double* d_quad, void* stream,
                                 char* errbuf, size_t errlen);
 
+/* evc_wait_selftest -- checks the failure detection of the streaming kernels
+ * without making the GPU fault or hang.  Every device-side wait of the library
+ * (on an mbarrier phase or a copy) gives up after a bounded number of SM clock
+ * cycles, records a timeout and lets the kernel return, and the call that
+ * launched it reports EVC_ETIMEOUT.  This entry runs one block whose wait can
+ * never complete (nothing arrives on its barrier) with a limit of limit_ms
+ * milliseconds (0 < limit_ms <= 2000, converted with the SM clock rate),
+ * synchronises the device and stores in *status the status that the wait
+ * produced: EVC_ETIMEOUT when the bounded wait gave up as designed.  Returns
+ * EVC_OK when the launch and the read-back succeeded (the context is still
+ * usable), EVC_EINVAL / EVC_ENOMEM / EVC_ECUDA otherwise.  It allocates and
+ * frees 4 bytes of device memory and uses the current device.  Not part of the
+ * paper: a property of this implementation. */
+int evc_wait_selftest(double limit_ms, int* status);
+
 const char* evc_last_error(const evc_ctx* ctx);
 void evc_destroy(evc_ctx* ctx);
 /* Library version, major*10000 + minor*100 + patch.                           */

@@ -55,14 +55,20 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Wait for the phase with the given parity to complete; false once `cycles`
+// SM clock cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long cycles)
 {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > cycles) return false;
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    return mbar_wait_for(bar, parity, kWaitCycles);
 }
 
 // bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned

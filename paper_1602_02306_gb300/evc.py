@@ -47,7 +47,8 @@ EXPORTED = [
     "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_set_option",
     "evc_get_profile", "evc_autotune", "evc_server_create", "evc_server_add_matrix", "evc_server_submit",
     "evc_server_poll", "evc_server_wait", "evc_server_stats", "evc_server_destroy",
-    "evc_gauss_quadrature_static", "evc_last_error", "evc_destroy", "evc_version",
+    "evc_gauss_quadrature_static", "evc_wait_selftest", "evc_last_error", "evc_destroy",
+    "evc_version",
 ]
 
 
@@ -116,6 +117,7 @@ def load(path: str | None = None):
             "evc_sync": (i32, [vp]),
             "evc_get_tridiag": (i32, [vp, dp, dp, ip]),
             "evc_autotune": (i32, [vp, i32, i32, i32, C.POINTER(evc_tuning)]),
+            "evc_wait_selftest": (i32, [d, C.POINTER(C.c_int)]),
             "evc_set_option": (i32, [vp, i32, i64]),
             "evc_get_profile": (i32, [vp, C.POINTER(evc_prof_rec), i32, ip]),
             "evc_server_create": (i32, [C.c_size_t, i32, i32, pp]),
@@ -259,6 +261,14 @@ def evc_autotune(ctx, nshift, nprobe, maxsteps):
     t = evc_tuning()
     _check(ctx, load().evc_autotune(ctx, nshift, nprobe, maxsteps, C.byref(t)))
     return {f: getattr(t, f) for f, _ in evc_tuning._fields_}
+
+
+def evc_wait_selftest(limit_ms):
+    """Run a wait that can never complete under a limit of limit_ms; returns the
+    status the bounded wait produced (EVC_ETIMEOUT when it gave up as designed)."""
+    st = C.c_int(-1)
+    _check(None, load().evc_wait_selftest(float(limit_ms), C.byref(st)))
+    return st.value
 
 
 def evc_get_profile(ctx):
