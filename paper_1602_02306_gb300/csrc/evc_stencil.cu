@@ -271,7 +271,14 @@ stencil_pass_kernel(KArgs a)
 // output of the 7-point stencil from 4R + 1 to R(PX + PY)/2 + 1 plus the
 // pointwise operands.  Per-point arithmetic and summation order are those of
 // stencil_pass_kernel.  N must be a multiple of PX and PY.
-constexpr int STP = 128;   // threads per block of the patch variant
+constexpr int STP1 = 128;  // threads per block of the patch variant, 7-point
+constexpr int STP2 = 128;  // threads per block of the patch variant, 13-point
+
+template <int R>
+__host__ __device__ constexpr int patch_threads()
+{
+    return R == 1 ? STP1 : STP2;
+}
 constexpr int DMAXP = 3;   // planes of loads in flight, patch variant (at most)
 constexpr int PTW = 8;     // patch-variant block tile width (points along x)
 
@@ -283,14 +290,15 @@ __host__ __device__ constexpr int patch_depth()
     constexpr int nl = 2 * R * (PX + PY) +
                        PX * PY * (1 + ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) +
                                   ((MASK & HAS_PP) ? 1 : 0));
-    constexpr int fit = 220 * 1024 / (nl * STP * 16) - 1;
+    constexpr int fit = 220 * 1024 / (nl * patch_threads<R>() * 16) - 1;
     return fit < DMAXP ? fit : DMAXP;
 }
 
 template <typename T, int R, int MASK, int PX, int PY>
-__global__ void __launch_bounds__(STP)
+__global__ void __launch_bounds__(patch_threads<R>())
 stencil_patch_kernel(KArgs a)
 {
+    constexpr int STP = patch_threads<R>();
     constexpr int DEPTHP = patch_depth<R, MASK, PX, PY>();
     static_assert(DEPTHP >= 1, "patch kernel slots do not fit shared memory");
     constexpr int W = 16 / sizeof(T);
@@ -488,6 +496,7 @@ void launch_patch(dim3 grid, cudaStream_t st, const KArgs& a)
 {
     constexpr int NB = 2 * R * (PX + PY);
     constexpr int NOP = ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) + ((MASK & HAS_PP) ? 1 : 0);
+    constexpr int STP = patch_threads<R>();
     constexpr size_t smem =
         (size_t)(patch_depth<R, MASK, PX, PY>() + 1) * (NB + PX * PY * (1 + NOP)) * STP * 16;
     static bool attr_set = false;
@@ -583,7 +592,7 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     bool ok;
     if (!jacobi && op.patch == 2 && N % 2 == 0) {
         // 2 x 2 patches: PTW x (2 TYP) points per block
-        constexpr int TYP = STP / LPP / (PTW / 2);
+        const int TYP = (op.order == 2 ? patch_threads<1>() : patch_threads<2>()) / LPP / (PTW / 2);
         dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb,
                 r.nchunk);
         ok = op.order == 2 ? launch_patch_masked<T, 1, 2, 2>(mask, pg, st, a)
