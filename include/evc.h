@@ -215,8 +215,9 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       itself stays FP32, so this measures the accuracy of
  *                       BF16 storage, not its bandwidth.  Default 0.
  *   EVC_OPT_REORTH_ROWS: rows per block of the reorthogonalisation kernels
- *                       (default 3456; at least 64, and at most max(ceil(n/1728),
- *                       min(ceil(n/64), 512)) blocks per chunk).  It sets the summation
+ *                       (default 0 = min(3456, max(64, ceil(n/64))); otherwise at
+ *                       least 64, and at most max(ceil(n/1728), min(ceil(n/64),
+ *                       512)) blocks per chunk).  It sets the summation
  *                       order of the dot products, so results may change in the
  *                       last bits; it never depends on how many columns a call
  *                       batches, so a column's result is the same alone or in

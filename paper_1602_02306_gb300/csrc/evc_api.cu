@@ -75,7 +75,7 @@ struct evc_ctx {
     double cheb_g = 1.0, cheb_sign = 1.0;   // |leading coefficient|^(1/d), its sign
     int cheb_form = EVC_CHEB_FACTORED;
     int basis_bf16 = 0;
-    int reorth_rows = 3456;       // rows per block of the reorthogonalisation kernels
+    int reorth_rows = 0;          // rows per block of the reorthogonalisation kernels (0: by n)
     int method = EVC_METHOD_LANCZOS;
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
@@ -134,11 +134,20 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Row blocks per chunk of the reorthogonalisation kernels.  It depends on n
 // only, never on how many chunks share the launch, so the summation order of
 // every dot product -- and therefore every result -- is the same whether a
-// column runs alone or batched with others.  3456 rows per block (54 tiles
-// of the update kernel) keeps each block's bulk-copy pipeline long; the
-// 64^3 Hamiltonian with four chunks gets 304 blocks, two per SM.
-int choose_nblk(int64_t n, int rows = 3456)
+// column runs alone or batched with others.  By default 3456 rows per block
+// (54 tiles of the update kernel) keeps each block's bulk-copy pipeline long
+// (the 64^3 Hamiltonian with four chunks gets 304 blocks, two per SM), and a
+// problem with fewer than 64 x 3456 rows gets 64 blocks per chunk of at least
+// 64 rows, so that small problems still spread over the GPU.
+int default_reorth_rows(int64_t n)
 {
+    const int64_t r = (n + 63) / 64;
+    return (int)std::min<int64_t>(3456, std::max<int64_t>(kMinReorthRows, r));
+}
+
+int choose_nblk(int64_t n, int rows)
+{
+    if (rows <= 0) rows = default_reorth_rows(n);
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + rows - 1) / rows, 65535));
 }
 
@@ -1404,7 +1413,7 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         return EVC_OK;
     }
     if (option == EVC_OPT_REORTH_ROWS) {
-        if (value < kMinReorthRows || value > ((int64_t)1 << 30))
+        if (value != 0 && (value < kMinReorthRows || value > ((int64_t)1 << 30)))
             return fail(ctx, EVC_EINVAL, "reorthogonalisation rows per block must be >= %d", kMinReorthRows);
         if (choose_nblk(ctx->n, (int)value) > reorth_max_blocks(ctx->n))
             return fail(ctx, EVC_EINVAL, "at most %d reorthogonalisation blocks per chunk for n = %lld",
@@ -1583,7 +1592,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
     // reorthogonalisation: rows per block
     {
         double best = 1e300;
-        int br = 3456;
+        int br = 0;
         int last_nblk = -1;
         for (int rows : {64, 128, 256, 512, 1024, 1728, 3456, 6912, 13824}) {
             const int nb = choose_nblk(ctx->n, rows);
@@ -1605,7 +1614,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
     res.stencil_zb = ctx->op == OP_STENCIL ? ctx->sten.zb : 0;
     res.stencil_patch = ctx->op == OP_STENCIL ? std::max(1, ctx->sten.patch) : 0;
     res.csr_threads = ctx->op == OP_CSR ? ctx->csr.threads : 0;
-    res.reorth_rows = ctx->reorth_rows;
+    res.reorth_rows = ctx->reorth_rows > 0 ? ctx->reorth_rows : default_reorth_rows(ctx->n);
     res.steps = kt;
     if (out) *out = res;
     return restore(EVC_OK);
