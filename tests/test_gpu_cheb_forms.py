@@ -22,11 +22,12 @@ def _lib():
     evc.load()
 
 
-def _count(N, order, prec, form, degree, shifts, m, k, h=0.3, tol=0.0):
+def _count(N, order, prec, form, degree, shifts, m, k, h=0.3, tol=0.0, patch=1):
     V = I.gaussian_wells(N, h, nwells=5, seed=1)
     with evc.Context.stencil(N, h, order, V, precision=prec) as ctx:
         ctx.set_precond(evc.EVC_PREC_CHEB_KINETIC, degree, 1.0)
         ctx.set_option(evc.EVC_OPT_CHEB_FORM, form)
+        ctx.set_option(evc.EVC_OPT_STENCIL_PATCH, patch)
         L, q, st = ctx.count_slices(shifts, m, k, tol=tol, seed=0)
     return V, L, q, st
 
@@ -56,9 +57,13 @@ def test_factored_mixed_within_half_of_oracle():
     assert np.max(np.abs(L - Lc)) < 0.05
 
 
-def test_factored_adaptive_stop_matches_oracle():
+@pytest.mark.parametrize("patch", [1, 2])
+def test_factored_adaptive_stop_matches_oracle(patch):
+    # chunks stop at different steps and leave the stencil grid on the device
     N, shifts = 10, list(np.linspace(-4.0, 2.0, 7))
-    V, L, q, st = _count(N, 2, evc.EVC_FP64, evc.EVC_CHEB_FACTORED, 8, shifts, 16, 30, tol=0.25)
+    V, L, q, st = _count(N, 2, evc.EVC_FP64, evc.EVC_CHEB_FACTORED, 8, shifts, 16, 30, tol=0.25,
+                         patch=patch)
+    assert len(set(st)) > 1
     P = O.Problem.stencil(N, 0.3, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
     qr, sr, Lr = O.count(P, shifts, 16, 30, tol=0.25, seed=0)
     assert list(st) == list(sr)
