@@ -95,7 +95,7 @@ class ClockSampler:
 
 _CHEB_FORM = [0]     # EVC_CHEB_FACTORED; --cheb-form clenshaw sets 1
 _METHOD = [0]        # EVC_METHOD_LANCZOS; --method arnoldi sets 1
-_SHAPES = {"patch": 0, "zb": 0}   # 0: library default
+_SHAPES = {"patch": 0, "zb": 0, "csr_threads": 0}   # 0: library default
 
 
 def _make_ctx(evc, W, precision, stream_ptr, V=None):
@@ -111,6 +111,8 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
     if W.precond == "cheb":
         evc.evc_set_option(ctx.h, evc.EVC_OPT_CHEB_FORM, _CHEB_FORM[0])
     evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, _METHOD[0])
+    if W.kind == "csr" and _SHAPES["csr_threads"]:
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_CSR_THREADS, _SHAPES["csr_threads"])
     if W.kind == "stencil":
         # fixed tile shapes (the autotuner, when it runs, starts from these)
         if _SHAPES["patch"]:
@@ -519,6 +521,8 @@ def main():
                     help="points per thread of the stencil pass (with --no-autotune)")
     ap.add_argument("--stencil-zb", type=int, default=0,
                     help="z planes per block of the stencil pass (with --no-autotune)")
+    ap.add_argument("--csr-threads", type=int, default=0, choices=[0, 128, 256, 512],
+                    help="threads per block of the CSR pass (with --no-autotune)")
     ap.add_argument("--method", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="estimator: preconditioned Lanczos (default) or the Arnoldi-type variant")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
@@ -530,6 +534,7 @@ def main():
     _CHEB_FORM[0] = 0 if args.cheb_form == "factored" else 1
     _METHOD[0] = 0 if args.method == "lanczos" else 1
     _SHAPES["patch"], _SHAPES["zb"] = args.stencil_patch, args.stencil_zb
+    _SHAPES["csr_threads"] = args.csr_threads
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":

@@ -108,9 +108,21 @@ def powerlaw_2m() -> Workload:
                     notes={"n": 2_000_000})
 
 
+def powerlaw_1m_profile() -> Workload:
+    """A smaller case of the same CSR pass for profiling: power-law rows as in
+    powerlaw_2m with n = 1,200,000 (each chunk's 32-column x vector, 154 MB,
+    is still larger than L2, so the gathers reach DRAM), 64 probes, 4 steps --
+    about 2.5 GB on the device."""
+    return Workload(name="powerlaw_1.2M_jacobi_m64_k4", kind="csr", shifts=[-0.5, 0.5],
+                    nprobe=64, maxsteps=4, precond="jacobi", prec_params=(1e-3, 0.0),
+                    csr_builder=lambda: I.powerlaw_symmetric(1_200_000, cap=2000, seed=2),
+                    notes={"n": 1_200_000})
+
+
 WORKLOADS = {
     "fd64": fd_hamiltonian_64,
     "laplace32": laplace32,
     "slicing96": batched_slicing_96,
     "powerlaw2m": powerlaw_2m,
+    "powerlaw1m": powerlaw_1m_profile,
 }
