@@ -239,7 +239,7 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       - tau| + eps)); Chebyshev: T = p_d(K)^2; identity), the
  *                       quadrature ||v||^2 Re(e_1^T h(H_k) e_1) with h = 1 on the
  *                       open left half-plane (Eq. arnoldi_quad), the same probes,
- *                       means and stop rule.  At most 64 steps; the Gauss rule
+ *                       means and stop rule.  At most 90 steps; the Gauss rule
  *                       only; evc_get_tridiag does not apply.  Per-probe values
  *                       may be negative (the weights are complex).  */
 enum {

@@ -77,8 +77,8 @@ struct Run {
 };
 
 // Longest Arnoldi run: the quadrature keeps three k x k FP64 matrices in
-// shared memory (evc_arnoldi.cu).
-constexpr int kArnoldiMaxSteps = 64;
+// shared memory (evc_arnoldi.cu): 195 KB at k = 90.
+constexpr int kArnoldiMaxSteps = 90;
 
 // Coefficients of one stencil pass (see evc_stencil.cu):
 //   st  = k1 * (L in)_offdiag + (k1*cd + k0 + [V_p] - [sigma_c]) * in_p

@@ -102,7 +102,7 @@ def test_arnoldi_limits():
     with evc.Context.stencil(8, 0.3, 2, V, precision=evc.EVC_FP64) as ctx:
         ctx.set_option(evc.EVC_OPT_METHOD, evc.EVC_METHOD_ARNOLDI)
         with pytest.raises(evc.EvcError):
-            ctx.count_slices([0.0], 8, 65)
+            ctx.count_slices([0.0], 8, 91)
         ctx.set_option(evc.EVC_OPT_QUADRATURE, evc.EVC_QUAD_GA)
         with pytest.raises(evc.EvcError):
             ctx.count_slices([0.0], 8, 10)
@@ -112,3 +112,13 @@ def test_arnoldi_limits():
             ctx.tridiag(8, 10)
         with pytest.raises(evc.EvcError):
             ctx.set_option(evc.EVC_OPT_METHOD, 2)
+
+
+def test_arnoldi_long_run_matches_oracle():
+    # 80 steps: H_80 in the quadrature kernel's shared memory
+    N, shifts, m, k = 10, [-1.0, 0.5], 8, 80
+    V = I.gaussian_wells(N, 0.3, nwells=4, seed=1)
+    L, q, st = _stencil(N, 2, V, evc.EVC_FP64, "identity", shifts, m, k)
+    P = O.Problem.stencil(N, 0.3, 2, V, O.PREC_NONE)
+    qr, sr, Lr = AR.count(P, shifts, m, k, seed=0)
+    assert np.max(np.abs(q - qr)) < 1e-7
