@@ -122,3 +122,20 @@ def test_arnoldi_long_run_matches_oracle():
     P = O.Problem.stencil(N, 0.3, 2, V, O.PREC_NONE)
     qr, sr, Lr = AR.count(P, shifts, m, k, seed=0)
     assert np.max(np.abs(q - qr)) < 1e-7
+
+
+def test_arnoldi_breakdown_at_p_distinct_eigenvalues():
+    # T = I and p distinct eigenvalues: the Arnoldi process stops at step p
+    # (h_{p+1,p} = 0) and the quadrature is exact, in both precisions
+    distinct = [-2.0, -0.5, 0.7, 1.5, 3.0]
+    A = I.random_symmetric_dense(64, seed=4, distinct=distinct)
+    csr = I.dense_to_csr(A)
+    w, U = np.linalg.eigh(A)
+    for prec in (evc.EVC_FP64, evc.EVC_MIXED):
+        with evc.Context.csr(csr, precision=prec) as ctx:
+            ctx.set_option(evc.EVC_OPT_METHOD, evc.EVC_METHOD_ARNOLDI)
+            L, q, st = ctx.count_slices([0.0], 4, 12, seed=0)
+        for j in range(4):
+            v = O.probe_vector(0, j, 64)
+            exact = float(np.sum((U[:, w < 0].T @ v) ** 2))
+            assert abs(q[0, j] - exact) < (1e-8 if prec == evc.EVC_FP64 else 1e-3)
