@@ -282,15 +282,21 @@ __host__ __device__ constexpr int patch_threads()
 constexpr int DMAXP = 3;   // planes of loads in flight, patch variant (at most)
 constexpr int PTW = 8;     // patch-variant block tile width (points along x)
 
-// Planes in flight of one patch-kernel instance: DMAXP, or fewer when its
-// slots (NL per plane per thread) would not fit 220 KB of shared memory.
+// Planes in flight of one patch-kernel instance (slots: NL per plane per
+// thread).  7-point (R = 1): DMAXP, or fewer when the slots would not fit one
+// block of 220 KB.  13-point (R = 2): as many as let two blocks share an SM
+// (113 KB each) -- measured 23% faster than a deeper pipeline with one block --
+// falling back to the one-block rule when not even one plane allows that.  For
+// R = 1 the two rules measured within 1%, the one-block rule ahead.
 template <int R, int MASK, int PX, int PY>
 __host__ __device__ constexpr int patch_depth()
 {
     constexpr int nl = 2 * R * (PX + PY) +
                        PX * PY * (1 + ((MASK & HAS_X) ? 1 : 0) + ((MASK & HAS_PREV) ? 1 : 0) +
                                   ((MASK & HAS_PP) ? 1 : 0));
-    constexpr int fit = 220 * 1024 / (nl * patch_threads<R>() * 16) - 1;
+    constexpr int two = 113 * 1024 / (nl * patch_threads<R>() * 16) - 1;
+    constexpr int one = 220 * 1024 / (nl * patch_threads<R>() * 16) - 1;
+    constexpr int fit = (R == 2 && two > 0) ? two : one;
     return fit < DMAXP ? fit : DMAXP;
 }
 
