@@ -229,6 +229,15 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       whose inner neighbours come from registers (fewer loads
  *                       per output; passes without Jacobi scaling and grids
  *                       with N even, else 1 is used).  Results agree to rounding.
+ *   EVC_OPT_STENCIL_GROUPS: stencil contexts: 1 (default) to 4.  The stencil
+ *                       passes of each step's operator application run as this
+ *                       many groups of column chunks, each group on its own
+ *                       stream (forked from and joined back into the context's
+ *                       stream, inside the captured graph), so that one group's
+ *                       passes fill the SMs another group's tail wave leaves
+ *                       idle.  At most one group per chunk.  Results are
+ *                       bitwise unchanged.  With profiling on, each segment is
+ *                       timed as one span record (see evc_prof_rec).
  *   EVC_OPT_CSR_THREADS: CSR contexts: threads per block of the CSR pass, 128,
  *                       256 (default) or 512.  Results are unchanged.
  *   EVC_OPT_METHOD    : EVC_METHOD_LANCZOS (default): Algorithms 1-2 on
@@ -254,7 +263,8 @@ enum {
     EVC_OPT_STENCIL_ZB = 9,
     EVC_OPT_CSR_THREADS = 10,
     EVC_OPT_METHOD = 11,
-    EVC_OPT_STENCIL_PATCH = 12
+    EVC_OPT_STENCIL_PATCH = 12,
+    EVC_OPT_STENCIL_GROUPS = 13
 };
 enum { EVC_METHOD_LANCZOS = 0, EVC_METHOD_ARNOLDI = 1 };
 enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };
@@ -276,17 +286,24 @@ enum {
 /* One kernel launch of the last call: its class, Lanczos step (0 = set-up),
  * device time in milliseconds (events on the context's stream; -1 when
  * profiling was off) and the compulsory HBM bytes of the launch (every
- * operand read once, every output written once, all chunks active).          */
+ * operand read once, every output written once, all chunks active).
+ * With stencil chunk groups (EVC_OPT_STENCIL_GROUPS > 1) the launches of a
+ * step's operator segment run concurrently on several streams: they carry
+ * ms = -1 and their group's share of the bytes, and one extra record with
+ * span = 1 covers the segment -- its wall time on the context's stream and
+ * the compulsory bytes of all its launches.  span = 0 for a launch.          */
 typedef struct {
     int32_t kind;
     int32_t step;
     double ms;
     double bytes;
+    int32_t span;
+    int32_t reserved;
 } evc_prof_rec;
 
-/* Launch list of the last call.  Writes min(cap, launches) records to recs
- * (may be NULL) and the number of kernel launches of one call to *nrec.
- * Synchronises the context's stream.                                          */
+/* Launch list of the last call.  Writes min(cap, records) records to recs
+ * (may be NULL) and the number of records of one call (launches plus span
+ * records) to *nrec.  Synchronises the context's stream.                     */
 int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
 
 /* evc_autotune -- the library's tile-shape autotuner.  Times short counts
@@ -294,7 +311,8 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  * the caller's launch shape) with a pair of timing events around every kernel,
  * and keeps, per kernel family, the fastest of
  *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB) times
- *                  points per thread 1 / 2x2 (EVC_OPT_STENCIL_PATCH),
+ *                  points per thread 1 / 2x2 (EVC_OPT_STENCIL_PATCH), then
+ *                  1 / 2 / 4 concurrent chunk groups (EVC_OPT_STENCIL_GROUPS),
  *   CSR pass:      threads per block 128 / 256 / 512 (EVC_OPT_CSR_THREADS),
  *   reorthogonalisation: rows per block 64 ... 13824 within the allowed
  *                  block counts (EVC_OPT_REORTH_ROWS),
@@ -308,6 +326,7 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
 typedef struct {
     int stencil_zb;      /* chosen z planes per block (stencil contexts), else 0 */
     int stencil_patch;   /* chosen points per thread, 1 or 2 (2 x 2 patch), else 0 */
+    int stencil_groups;  /* chosen concurrent chunk groups (stencil contexts), else 0 */
     int csr_threads;     /* chosen threads per block (CSR contexts), else 0 */
     int reorth_rows;     /* chosen rows per block of the reorthogonalisation */
     int steps;           /* Lanczos steps of each timing count */

@@ -76,6 +76,10 @@ struct evc_ctx {
     int cheb_form = EVC_CHEB_FACTORED;
     int basis_bf16 = 0;
     int reorth_rows = 0;          // rows per block of the reorthogonalisation kernels (0: by n)
+    // stencil operator segment of a step split into this many chunk groups on
+    // concurrent streams (1: one stream); aux[g - 1] is the stream of group g
+    int sten_groups = 1;
+    cudaStream_t aux[kMaxStencilGroups - 1] = {};
     int method = EVC_METHOD_LANCZOS;
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
@@ -93,9 +97,15 @@ struct evc_ctx {
     cudaEvent_t param_ev = nullptr;
     // launch list of the enqueued sequence (with timing events when profiling)
     bool profile = false;
-    // bytes of a launch = fixed + per_chunk * (chunks active in that step)
-    struct Rec { int kind, step; double fixed, per_chunk; cudaEvent_t e0, e1; };
+    // bytes of a launch = fixed + per_chunk * (chunks active in that step);
+    // span = 1: not a launch but the interval of a concurrent chunk-group
+    // segment, whose launches carry no events of their own
+    struct Rec { int kind, step; double fixed, per_chunk; cudaEvent_t e0, e1; int span; };
     std::vector<Rec> recs;
+    bool in_span = false;         // enqueueing inside a chunk-group segment
+    bool span_sum = false;        // ... the group whose launches the span record sums
+    double span_frac = 1.0;       // share of the chunks in the current group
+    double span_fixed = 0.0, span_per = 0.0;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
     // graph
@@ -460,8 +470,17 @@ cudaEvent_t pool_event(evc_ctx* ctx)
 template <class F>
 int rec(evc_ctx* ctx, int kind, int step, double fixed, double per_chunk, F&& launch)
 {
-    evc_ctx::Rec r{kind, step, fixed, per_chunk, nullptr, nullptr};
-    if (ctx->profile) {
+    evc_ctx::Rec r{kind, step, fixed, per_chunk, nullptr, nullptr, 0};
+    if (ctx->in_span) {
+        // concurrent with the other groups: timed as one span, bytes summed
+        // once over the whole chunk range
+        if (ctx->span_sum) {
+            ctx->span_fixed += fixed;
+            ctx->span_per += per_chunk;
+        }
+        r.fixed = fixed * ctx->span_frac;
+        r.per_chunk = per_chunk * ctx->span_frac;
+    } else if (ctx->profile) {
         r.e0 = pool_event(ctx);
         r.e1 = pool_event(ctx);
         if (!r.e0 || !r.e1) return fail(ctx, EVC_ECUDA, "cudaEventCreate failed");
@@ -472,8 +491,74 @@ int rec(evc_ctx* ctx, int kind, int step, double fixed, double per_chunk, F&& la
     if (e != cudaSuccess)
         return fail(ctx, EVC_ECUDA, "kernel launch (class %d, step %d): %s", kind, step,
                     cudaGetErrorString(e));
-    if (ctx->profile) CU(cudaEventRecordWithFlags(r.e1, ctx->stream, cudaEventRecordExternal));
+    if (r.e1) CU(cudaEventRecordWithFlags(r.e1, ctx->stream, cudaEventRecordExternal));
     ctx->recs.push_back(r);
+    return EVC_OK;
+}
+
+// Enqueue body() -- the stencil launches of one operator application -- once
+// per chunk group, each group on its own stream, forked from and joined back
+// into the context's stream.  The chunks of a step are independent until the
+// reorthogonalisation, so the groups' launches overlap and the tail wave of
+// one group's pass runs beside the next pass of another instead of leaving
+// SMs idle.  Every chunk is computed by the same kernels as without groups,
+// so results are bitwise the same.  When profiling, the segment is one span
+// record (kind `kind`) timed on the context's stream.
+template <class F>
+int grouped(evc_ctx* ctx, const Run& r, int kind, int step, F&& body)
+{
+    const int G = std::min(ctx->sten_groups, r.nchunk);
+    if (G <= 1 || ctx->in_span) return body();
+    cudaStream_t s0 = ctx->stream;
+    for (int g = 1; g < G; ++g)
+        if (!ctx->aux[g - 1]) CU(cudaStreamCreateWithFlags(&ctx->aux[g - 1], cudaStreamNonBlocking));
+    cudaEvent_t fork = pool_event(ctx);
+    if (!fork) return fail(ctx, EVC_ECUDA, "cudaEventCreate failed");
+    evc_ctx::Rec span{kind, step, 0.0, 0.0, nullptr, nullptr, 1};
+    if (ctx->profile) {
+        span.e0 = pool_event(ctx);
+        span.e1 = pool_event(ctx);
+        if (!span.e0 || !span.e1) return fail(ctx, EVC_ECUDA, "cudaEventCreate failed");
+        CU(cudaEventRecordWithFlags(span.e0, s0, cudaEventRecordExternal));
+    }
+    CU(cudaEventRecord(fork, s0));
+    ctx->in_span = true;
+    ctx->span_fixed = ctx->span_per = 0.0;
+    int rc = EVC_OK;
+    for (int g = 0; g < G && !rc; ++g) {
+        const int c0 = (int)((int64_t)r.nchunk * g / G), c1 = (int)((int64_t)r.nchunk * (g + 1) / G);
+        cudaStream_t sg = g == 0 ? s0 : ctx->aux[g - 1];
+        if (g > 0) {
+            cudaError_t e = cudaStreamWaitEvent(sg, fork, 0);
+            if (e != cudaSuccess) {
+                rc = fail(ctx, EVC_ECUDA, "stream fork: %s", cudaGetErrorString(e));
+                break;
+            }
+        }
+        ctx->stream = sg;
+        ctx->sten.c0 = c0;
+        ctx->sten.cn = c1 - c0;
+        ctx->span_sum = g == 0;
+        ctx->span_frac = (double)(c1 - c0) / r.nchunk;
+        rc = body();
+        if (g > 0) {
+            // join: the context's stream waits for this group (also after an
+            // error, so that a capture ends with every stream joined)
+            cudaEvent_t join = pool_event(ctx);
+            cudaError_t e = join ? cudaEventRecord(join, sg) : cudaErrorMemoryAllocation;
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, join, 0);
+            if (e != cudaSuccess && !rc) rc = fail(ctx, EVC_ECUDA, "stream join: %s", cudaGetErrorString(e));
+        }
+    }
+    ctx->stream = s0;
+    ctx->sten.c0 = ctx->sten.cn = 0;
+    ctx->in_span = ctx->span_sum = false;
+    ctx->span_frac = 1.0;
+    if (rc) return rc;
+    span.fixed = ctx->span_fixed;
+    span.per_chunk = ctx->span_per;
+    if (span.e1) CU(cudaEventRecordWithFlags(span.e1, s0, cudaEventRecordExternal));
+    if (ctx->profile) ctx->recs.push_back(span);
     return EVC_OK;
 }
 
@@ -675,17 +760,20 @@ int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
         p.useSigma = 1;
         p.out = wout;
         p.out_cs = r.chunk_stride;
-        rc = stencil<T>(ctx, r, i, p, false);
-        if (!rc && ctx->prec == EVC_PREC_CHEB_KINETIC) {
-            T* W0 = static_cast<T*>(work);
-            T* W1 = W0 + (int64_t)r.nchunk * vstride;
-            T* W2 = W1 + (int64_t)r.nchunk * vstride;
-            rc = enqueue_cheb<T>(ctx, r, i, wout, r.chunk_stride, nullptr, W0, W1, W2, vstride,
-                                 nullptr, 0, nullptr);
-            if (!rc)
-                rc = enqueue_cheb<T>(ctx, r, i, W2, vstride, nullptr, W0, W1, wout, r.chunk_stride,
-                                     nullptr, 0, nullptr);
-        }
+        rc = grouped(ctx, r, EVC_K_STENCIL, i, [&]() -> int {
+            int rc2 = stencil<T>(ctx, r, i, p, false);
+            if (!rc2 && ctx->prec == EVC_PREC_CHEB_KINETIC) {
+                T* W0 = static_cast<T*>(work);
+                T* W1 = W0 + (int64_t)r.nchunk * vstride;
+                T* W2 = W1 + (int64_t)r.nchunk * vstride;
+                rc2 = enqueue_cheb<T>(ctx, r, i, wout, r.chunk_stride, nullptr, W0, W1, W2,
+                                      vstride, nullptr, 0, nullptr);
+                if (!rc2)
+                    rc2 = enqueue_cheb<T>(ctx, r, i, W2, vstride, nullptr, W0, W1, wout,
+                                          r.chunk_stride, nullptr, 0, nullptr);
+            }
+            return rc2;
+        });
     }
     if (!rc && uses_jac(ctx))
         rc = rec(ctx, EVC_K_JACOBI, i, (double)r.S * r.n * sizeof(T), 2.0 * vchunk,
@@ -731,24 +819,26 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             T* W0 = static_cast<T*>(work);
             T* W1 = W0 + (int64_t)r.nchunk * vstride;
             T* W2 = W1 + (int64_t)r.nchunk * vstride;
-            // u = M q_i into W2
-            rc = enqueue_cheb<T>(ctx, r, i, qi, r.chunk_stride, si, W0, W1, W2, vstride, nullptr,
-                                 0, nullptr);
-            if (rc) return rc;
-            // t = (H - sigma I) u into W0
-            StencilPass p{};
-            p.in = W2;
-            p.in_cs = vstride;
-            p.k1 = 1.0;
-            p.useV = 1;
-            p.useSigma = 1;
-            p.out = W0;
-            p.out_cs = vstride;
-            rc = stencil<T>(ctx, r, i, p, false);
-            if (rc) return rc;
-            // w = M t - beta_i q_{i-1} into slot i
-            rc = enqueue_cheb<T>(ctx, r, i, W0, vstride, nullptr, W1, W2, wout, r.chunk_stride,
-                                 qprev, r.chunk_stride, r.ppc);
+            rc = grouped(ctx, r, EVC_K_STENCIL, i, [&]() -> int {
+                // u = M q_i into W2
+                int rc2 = enqueue_cheb<T>(ctx, r, i, qi, r.chunk_stride, si, W0, W1, W2, vstride,
+                                          nullptr, 0, nullptr);
+                if (rc2) return rc2;
+                // t = (H - sigma I) u into W0
+                StencilPass p{};
+                p.in = W2;
+                p.in_cs = vstride;
+                p.k1 = 1.0;
+                p.useV = 1;
+                p.useSigma = 1;
+                p.out = W0;
+                p.out_cs = vstride;
+                rc2 = stencil<T>(ctx, r, i, p, false);
+                if (rc2) return rc2;
+                // w = M t - beta_i q_{i-1} into slot i
+                return enqueue_cheb<T>(ctx, r, i, W0, vstride, nullptr, W1, W2, wout,
+                                       r.chunk_stride, qprev, r.chunk_stride, r.ppc);
+            });
         } else {
             StencilPass p{};
             p.in = qi;
@@ -762,7 +852,8 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             p.pp = qprev;
             p.pp_cs = r.chunk_stride;
             p.ppc = qprev ? r.ppc : nullptr;
-            rc = stencil<T>(ctx, r, i, p, uses_jac(ctx));
+            rc = grouped(ctx, r, EVC_K_STENCIL, i,
+                         [&]() -> int { return stencil<T>(ctx, r, i, p, uses_jac(ctx)); });
         }
         if (rc) return rc;
         rc = rec(ctx, EVC_K_DOTS, i, 0.0, vchunk * (i + 1), [&] { return launch_dots<T>(r, i, st); });
@@ -1048,6 +1139,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->cheb_form = src->cheb_form;
     c->basis_bf16 = src->basis_bf16;
     c->reorth_rows = src->reorth_rows;
+    c->sten_groups = src->sten_groups;
     c->method = src->method;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
@@ -1439,6 +1531,15 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         drop_graph(ctx);
         return EVC_OK;
     }
+    if (option == EVC_OPT_STENCIL_GROUPS) {
+        if (ctx->op != OP_STENCIL) return fail(ctx, EVC_EINVAL, "not a stencil context");
+        if (value < 1 || value > kMaxStencilGroups)
+            return fail(ctx, EVC_EINVAL, "stencil chunk groups must be in [1, %d]", kMaxStencilGroups);
+        ctx->sten_groups = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
     if (option == EVC_OPT_CSR_THREADS) {
         if (ctx->op != OP_CSR) return fail(ctx, EVC_EINVAL, "not a CSR context");
         if (value != 128 && value != 256 && value != 512)
@@ -1500,6 +1601,8 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec)
         float ms = -1.0f;
         if (r.e0 && r.e1) CU(cudaEventElapsedTime(&ms, r.e0, r.e1));
         recs[i].ms = ms;
+        recs[i].span = r.span;
+        recs[i].reserved = 0;
     }
     return EVC_OK;
 }
@@ -1513,7 +1616,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
     const std::vector<double> shifts(nshift, 0.0);
     const bool prof0 = ctx->profile;
     const int rows0 = ctx->reorth_rows, zb0 = ctx->sten.zb, nt0 = ctx->csr.threads,
-              pa0 = ctx->sten.patch;
+              pa0 = ctx->sten.patch, gr0 = ctx->sten_groups;
     auto restore = [&](int rc) {
         ctx->profile = prof0;
         ++ctx->prec_version;
@@ -1522,6 +1625,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
             ctx->reorth_rows = rows0;
             ctx->sten.zb = zb0;
             ctx->sten.patch = pa0;
+            ctx->sten_groups = gr0;
             ctx->csr.threads = nt0;
         }
         return rc;
@@ -1575,6 +1679,21 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
         }
         ctx->sten.zb = bz;
         ctx->sten.patch = bp;
+        // concurrent chunk groups of the operator segment (at most one per chunk)
+        const int nchunk = (int)(((int64_t)nshift * nprobe + CW - 1) / CW);
+        best = 1e300;
+        int bg = 1;
+        for (int g : {1, 2, 4}) {
+            if (g > 1 && g > nchunk) continue;
+            ctx->sten_groups = g;
+            double t;
+            if ((rc = measure(1u << EVC_K_STENCIL, t))) return restore(rc);
+            if (t < best) {
+                best = t;
+                bg = g;
+            }
+        }
+        ctx->sten_groups = bg;
     } else {
         double best = 1e300;
         int bt = 256;
@@ -1613,6 +1732,7 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
     if (rc) return restore(rc);
     res.stencil_zb = ctx->op == OP_STENCIL ? ctx->sten.zb : 0;
     res.stencil_patch = ctx->op == OP_STENCIL ? std::max(1, ctx->sten.patch) : 0;
+    res.stencil_groups = ctx->op == OP_STENCIL ? ctx->sten_groups : 0;
     res.csr_threads = ctx->op == OP_CSR ? ctx->csr.threads : 0;
     res.reorth_rows = ctx->reorth_rows > 0 ? ctx->reorth_rows : default_reorth_rows(ctx->n);
     res.steps = kt;
@@ -1642,6 +1762,8 @@ void evc_destroy(evc_ctx* ctx)
     if (ctx->pinres) cudaFreeHost(ctx->pinres);
     if (ctx->param_ev) cudaEventDestroy(ctx->param_ev);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+    for (cudaStream_t s : ctx->aux)
+        if (s) cudaStreamDestroy(s);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -104,7 +104,11 @@ struct StencilOp {
     const void* V;          // T[n]
     int zb;                 // z planes per block (tuned; 0 = 32)
     int patch;              // points per thread: 1 (default) or 2 = a 2 x 2 patch (tuned)
+    int c0, cn;             // chunks c0 .. c0+cn-1 of the launch (cn = 0: every chunk)
 };
+
+// Most concurrent chunk groups of the stencil operator (EVC_OPT_STENCIL_GROUPS).
+constexpr int kMaxStencilGroups = 4;
 
 struct CsrOp {
     int64_t n, nnz;

@@ -580,17 +580,35 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     constexpr int LPP = CW / W;
     constexpr int TX = 8;
     constexpr int TY = STH / LPP / TX;
+    // a chunk range is a view: every per-chunk pointer moves to chunk c0 and
+    // the kernels see chunks 0 .. cn-1 of it (Jacobi scales and V are indexed
+    // by shift and point, not by chunk)
+    const int c0 = op.cn > 0 ? op.c0 : 0;
+    const int cn = op.cn > 0 ? op.cn : r.nchunk;
+    if (c0 < 0 || c0 + cn > r.nchunk) return cudaErrorInvalidValue;
+    auto at = [&](const void* q, int64_t cs) -> const void* {
+        return q ? static_cast<const void*>(static_cast<const T*>(q) + (int64_t)c0 * cs) : q;
+    };
+    auto atc = [&](const double* q) { return q ? q + (int64_t)c0 * CW : q; };
     KArgs a;
     a.p = p;
+    a.p.in = at(p.in, p.in_cs);
+    a.p.x = at(p.x, p.x_cs);
+    a.p.prev = at(p.prev, p.prev_cs);
+    a.p.pp = at(p.pp, p.pp_cs);
+    a.p.out = const_cast<void*>(at(p.out, p.out_cs));
+    a.p.insc = atc(p.insc);
+    a.p.xs = atc(p.xs);
+    a.p.ppc = atc(p.ppc);
     a.op = op;
-    a.shift_of = r.shift_of;
-    a.sigma = r.sigma;
+    a.shift_of = r.shift_of + (int64_t)c0 * CW;
+    a.sigma = atc(r.sigma);
     a.jac = r.jac;
-    a.chunk_active = r.chunk_active;
+    a.chunk_active = r.chunk_active + c0;
     a.n = r.n;
     const int N = op.N;
     const int zb = op.zb > 0 ? op.zb : ZB;
-    dim3 grid(((N + TX - 1) / TX) * ((N + TY - 1) / TY), (N + zb - 1) / zb, r.nchunk);
+    dim3 grid(((N + TX - 1) / TX) * ((N + TY - 1) / TY), (N + zb - 1) / zb, cn);
     // V and the per-column shift always enter together (the H - sigma I pass)
     if (p.useV != p.useSigma) return cudaErrorInvalidValue;
     const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |
@@ -599,8 +617,7 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     if (!jacobi && op.patch == 2 && N % 2 == 0) {
         // 2 x 2 patches: PTW x (2 TYP) points per block
         const int TYP = (op.order == 2 ? patch_threads<1>() : patch_threads<2>()) / LPP / (PTW / 2);
-        dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb,
-                r.nchunk);
+        dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb, cn);
         ok = op.order == 2 ? launch_patch_masked<T, 1, 2, 2>(mask, pg, st, a)
                            : launch_patch_masked<T, 2, 2, 2>(mask, pg, st, a);
         if (!ok) return cudaErrorInvalidValue;

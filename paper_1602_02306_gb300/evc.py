@@ -32,6 +32,7 @@ EVC_OPT_BASIS_BF16 = 7
 EVC_OPT_REORTH_ROWS, EVC_OPT_STENCIL_ZB, EVC_OPT_CSR_THREADS = 8, 9, 10
 EVC_OPT_METHOD = 11
 EVC_OPT_STENCIL_PATCH = 12
+EVC_OPT_STENCIL_GROUPS = 13
 EVC_METHOD_LANCZOS, EVC_METHOD_ARNOLDI = 0, 1
 EVC_CHEB_FACTORED, EVC_CHEB_CLENSHAW = 0, 1
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1
@@ -65,11 +66,13 @@ class evc_csr(C.Structure):
 
 
 class evc_prof_rec(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("step", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double)]
+    _fields_ = [("kind", C.c_int32), ("step", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double),
+                ("span", C.c_int32), ("reserved", C.c_int32)]
 
 
 class evc_tuning(C.Structure):
-    _fields_ = [("stencil_zb", C.c_int), ("stencil_patch", C.c_int), ("csr_threads", C.c_int),
+    _fields_ = [("stencil_zb", C.c_int), ("stencil_patch", C.c_int), ("stencil_groups", C.c_int),
+                ("csr_threads", C.c_int),
                 ("reorth_rows", C.c_int),
                 ("steps", C.c_int), ("ms_before", C.c_double), ("ms_after", C.c_double)]
 
@@ -272,13 +275,14 @@ def evc_wait_selftest(limit_ms):
 
 
 def evc_get_profile(ctx):
-    """Launch list of the last call: list of (kind, step, ms, bytes)."""
+    """Launch list of the last call: list of (kind, step, ms, bytes, span);
+    span = 1 marks the record that times a concurrent chunk-group segment."""
     lib = load()
     n = C.c_int(0)
     _check(ctx, lib.evc_get_profile(ctx, None, 0, C.byref(n)))
     recs = (evc_prof_rec * max(1, n.value))()
     _check(ctx, lib.evc_get_profile(ctx, recs, n.value, C.byref(n)))
-    return [(r.kind, r.step, r.ms, r.bytes) for r in recs[:n.value]]
+    return [(r.kind, r.step, r.ms, r.bytes, r.span) for r in recs[:n.value]]
 
 
 EVC_STATIC_QUAD_MAX = 262144

@@ -42,3 +42,63 @@ def test_null_context_is_rejected_without_gpu(lib):
     assert lib.evc_count(None, 0.0, 1.0, 4, 4, 0.0, 0, None, None, None) == evc.EVC_EINVAL
     assert lib.evc_workspace_bytes(None, 1, 1, 1) == 0
     assert lib.evc_last_error(None) == b"null context"
+
+
+def _header_constants():
+    src = open(os.path.join(ROOT, "include", "evc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"(EVC_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    for name, val in re.findall(r"#define\s+(EVC_[A-Z0-9_]+)\s+(-?\d+)", src):
+        consts[name] = int(val)
+    return consts
+
+
+def _header_structs():
+    src = open(os.path.join(ROOT, "include", "evc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return re.findall(r"typedef struct\s*\{(.*?)\}\s*(evc_[a-z_]+)\s*;", src, flags=re.S)
+
+
+def test_binding_constants_match_the_header():
+    consts = _header_constants()
+    assert len(consts) > 30
+    for name, val in consts.items():
+        assert getattr(evc, name, None) == val, name
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    # sizes and field offsets as a C compiler lays the header's structs out,
+    # against the ctypes mirrors of the binding
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = _header_structs()
+    assert {n for _, n in structs} >= {"evc_csr", "evc_prof_rec", "evc_tuning", "evc_result",
+                                        "evc_server_counters"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "evc.h"', "int main(void) {"]
+    for body, name in structs:
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*;", body):
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = 0
+    for line in out.splitlines():
+        name, field, val = line.split()
+        cls = getattr(evc, name)
+        if field == "size":
+            assert ctypes.sizeof(cls) == int(val), name
+        else:
+            assert getattr(cls, field).offset == int(val), (name, field)
+        seen += 1
+    assert seen > 30

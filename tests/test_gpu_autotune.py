@@ -68,6 +68,8 @@ def test_autotune_choices_and_parity():
         t = ctx.autotune(len(shifts), m, k)
         assert t["stencil_zb"] in (16, 30) and t["csr_threads"] == 0
         assert t["stencil_patch"] in (1, 2)
+        assert t["stencil_groups"] in (1, 2, 4)     # 80 columns: 3 chunks, so at most 2 groups
+        assert t["stencil_groups"] <= 3
         assert t["reorth_rows"] in (64, 128, 256, 512, 1024, 1728, 3456, 6912, 13824)
         assert t["ms_before"] > 0 and t["ms_after"] > 0 and t["steps"] == 6
         q = ctx.count_slices(shifts, m, k)[1]
