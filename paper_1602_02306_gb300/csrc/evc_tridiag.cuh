@@ -45,30 +45,39 @@ __device__ inline double tridiag_quadrature_inplace(double* dp, double* ep, doub
         const double eh = e[hi - 1];
         const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * sqrt(dl * dl + eh * eh);
         const double mu = d[hi] - eh * eh / den;
-        // implicit QR step on [lo, hi]: chase the bulge down the band
-        double xv = d[lo] - mu, yv = e[lo];
-        double bulge = 0.0;
+        // implicit QR step on [lo, hi]: chase the bulge down the band.  The
+        // entries one rotation hands to the next (d_t, e_t, z_t, the bulge)
+        // stay in registers; only the untouched d_{t+1}, e_{t+1}, z_{t+1} are
+        // loaded, off the dependency chain, and the chain's last values are
+        // stored once after the sweep.  The eigensolve is a chain of dependent
+        // FP64 operations, so its latency is the cost.
+        double a = d[lo], b = e[lo], zt = z[lo];
+        double xv = a - mu, yv = b;
         for (int t = lo; t < hi; ++t) {
+            const double dd = d[t + 1], zn = z[t + 1];
+            const double en = t + 1 < hi ? e[t + 1] : 0.0;
             // Lanczos coefficients are O(||C||): no scaling against overflow needed
-            const double rr = sqrt(xv * xv + yv * yv);
-            const double inv = rr == 0.0 ? 0.0 : 1.0 / rr;
-            const double cs = rr == 0.0 ? 1.0 : xv * inv;
-            const double sn = yv * inv;
-            if (t > lo) e[t - 1] = rr;                    // (t, t-1) after the rotation
-            const double a = d[t], b = e[t], dd = d[t + 1];
-            d[t] = cs * cs * a + 2.0 * cs * sn * b + sn * sn * dd;
-            d[t + 1] = sn * sn * a - 2.0 * cs * sn * b + cs * cs * dd;
-            e[t] = cs * sn * (dd - a) + (cs * cs - sn * sn) * b;
-            if (t + 1 < hi) {
-                bulge = sn * e[t + 1];
-                e[t + 1] = cs * e[t + 1];
+            const double s2 = xv * xv + yv * yv;
+            double cs = 1.0, sn = 0.0, rr = 0.0;
+            if (s2 > 0.0) {
+                const double inv = rsqrt(s2);
+                cs = xv * inv;
+                sn = yv * inv;
+                rr = s2 * inv;
             }
-            const double z0 = z[t], z1 = z[t + 1];
-            z[t] = cs * z0 + sn * z1;
-            z[t + 1] = -sn * z0 + cs * z1;
-            xv = e[t];
-            yv = bulge;
+            if (t > lo) e[t - 1] = rr;                    // (t, t-1) after the rotation
+            d[t] = cs * cs * a + 2.0 * cs * sn * b + sn * sn * dd;
+            const double dn = sn * sn * a - 2.0 * cs * sn * b + cs * cs * dd;
+            xv = cs * sn * (dd - a) + (cs * cs - sn * sn) * b;   // new e_t
+            yv = sn * en;                                        // bulge at (t+2, t)
+            z[t] = cs * zt + sn * zn;
+            zt = -sn * zt + cs * zn;
+            a = dn;
+            b = cs * en;                                         // new e_{t+1}
         }
+        d[hi] = a;
+        e[hi - 1] = xv;
+        z[hi] = zt;
     }
     double s = 0.0;
     for (int t = 0; t < k; ++t)

@@ -1,7 +1,6 @@
 """The request server: continuous admission by HBM footprint, merged
 launches, overlapping slots, and results that do not depend on the mix."""
 import threading
-import time
 
 import numpy as np
 import pytest
@@ -34,7 +33,12 @@ def _matrices():
 
 def test_result_same_alone_and_in_the_mix():
     ctxs = _matrices()
-    srv = evc.evc_server_create(8 << 30, slots=3, max_batch=8)
+    # a larger grid for the long counts that hold the slots
+    Vb = I.gaussian_wells(40, 0.3, nwells=4, seed=1)
+    big = evc.Context.stencil(40, 0.3, 2, Vb, precision=evc.EVC_MIXED)
+    big.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+    ctxs.append(big)
+    srv = evc.evc_server_create(24 << 30, slots=3, max_batch=8)
     try:
         mids = [evc.evc_server_add_matrix(srv, c.h) for c in ctxs]
         probe = dict(matrix_id=mids[1], xi=-2.0, eta=0.5, nprobe=32, maxsteps=20, tol=0.25, seed=7)
@@ -42,8 +46,12 @@ def test_result_same_alone_and_in_the_mix():
         t = evc.evc_server_submit(srv, **probe, quad_buf=alone)
         rc, ra = evc.evc_server_wait(srv, t)
         assert rc == evc.EVC_OK and ra["batch_size"] == 1
+        # every slot busy with a long count (distinct seeds: no two share a
+        # launch), so that the requests below wait and are merged whatever
+        # the timing
+        blockers = [evc.evc_server_submit(srv, mids[3], -1.0, 1.0, 64, 80, 0.0, 11 + j)
+                    for j in range(3)]
         # now the same request among many others, submitted from two threads
-        rng = np.random.default_rng(0)
         bufs, tickets = [], []
         lock = threading.Lock()
 
@@ -62,7 +70,6 @@ def test_result_same_alone_and_in_the_mix():
                                                32, 20, 0.25, 7)
                     with lock:
                         tickets.append(("other", tk))
-                time.sleep(float(g.uniform(0, 0.002)))
 
         th = [threading.Thread(target=submitter, args=(s,)) for s in (1, 2)]
         for x in th:
@@ -74,8 +81,11 @@ def test_result_same_alone_and_in_the_mix():
             rc, r = evc.evc_server_wait(srv, tk)
             assert rc == evc.EVC_OK
             res[tk] = (kind, r)
+        for tk in blockers:
+            rc, r = evc.evc_server_wait(srv, tk)
+            assert rc == evc.EVC_OK and r["batch_size"] == 1
         st = evc.evc_server_stats(srv)
-        assert st["completed"] == 1 + len(tickets)
+        assert st["completed"] == 1 + len(tickets) + len(blockers)
         assert st["merged"] > 0                      # requests did share launches
         merged_probe = [r for kind, r in res.values() if kind == "probe" and r["batch_size"] > 1]
         assert merged_probe, "the repeated request never ran inside a batch"
