@@ -176,6 +176,8 @@ def _attach_traffic(roof):
     roof["traffic_launch"] = d["launch"]
     roof["traffic_launch_algorithmic_bytes"] = d["algorithmic_bytes"]
     roof["traffic_source"] = d["profile"]
+    if "note" in d:
+        roof["traffic_note"] = d["note"]
 
 
 def run_ours(args):
