@@ -239,8 +239,9 @@ def run_ours(args):
     ms_mixed, L_mixed, steps_mixed = timed(ctx, args.steps, args.warmup, profile=False)
     clk = clocks.stop()
     # per-kernel device times: one more count of the same workload, replayed
-    # with a pair of timing events around every kernel (kept out of the timed
-    # region above, whose events see only the whole counts)
+    # with a pair of timing events around every kernel, or around each step's
+    # stencil segment when its chunk groups run concurrently (kept out of the
+    # timed region above, whose events see only the whole counts)
     timed(ctx, 1, 0, profile=True)
     recs = evc.evc_get_profile(ctx.h)
     launches_per_step = sum(1 for r in recs if not r[4])   # span records are not launches
