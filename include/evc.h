@@ -458,6 +458,31 @@ void evc_destroy(evc_ctx* ctx);
 /* Library version, major*10000 + minor*100 + patch.                           */
 int evc_version(void);
 
+/* evc_cheb_kinetic -- host only, no device work: the kinetic-energy
+ * Chebyshev preconditioner M = p_d(K), K = -1/2 Lap_h + cI, exactly as
+ * evc_set_precond(ctx, EVC_PREC_CHEB_KINETIC, degree, c) builds it for a
+ * periodic stencil of this order (2: 7-point, 4: 13-point) and spacing h
+ * (Sec. 6, the kinetic-energy preconditioning of the numerical examples):
+ * p_d interpolates x^(-1/2) at the d+1 Chebyshev points of the first kind on
+ * [a, b] = [c, c + 6/h^2] (order 2) or [c, c + 8/h^2] (order 4), the bounds of
+ * spec(K) from the stencil's symbol.
+ *   info[5]    out: a, b, min of p_d over the exact spectrum of K on an N^3
+ *              grid (0 when N = 0: not evaluated; evc_set_precond rejects a
+ *              grid where it is not > 0), g, sign;
+ *   coef[d+1]  out: p_d(x) = sum_j coef[j] T_j((2x - a - b)/(b - a));
+ *   factors[3*d], *nfac  out: the factored form the stencil passes apply,
+ *              p_d(x) = sign * prod over factors, a factor (re, im, 1) being
+ *              g^2 ((x - re)^2 + im^2) (a conjugate pair of roots) and (r, 0, 0)
+ *              being g (x - r) (a real root); pairs first, each group by
+ *              ascending re.  *nfac = 0 when the factored product fails to
+ *              reproduce the series to 1e-9 relative on [a, b] (the library
+ *              then uses Clenshaw's recurrence).
+ * All buffers are caller-owned host memory.  Returns EVC_OK, or EVC_EINVAL
+ * for a null buffer, N < 0, an order other than 2 / 4, h <= 0, a degree
+ * outside [1, 32] or c <= 0. */
+int evc_cheb_kinetic(int order, double h, int degree, double c, int N, double* info,
+                     double* coef, double* factors, int* nfac);
+
 #ifdef __cplusplus
 }
 #endif

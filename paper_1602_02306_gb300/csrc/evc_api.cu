@@ -454,6 +454,50 @@ int evc::cheb_coefficients(int degree, double a, double b, double* coef)
 
 namespace {
 
+// The kinetic Chebyshev preconditioner M = p_d(K) of a periodic stencil of
+// this order and spacing, K = -1/2 Lap_h + cI: its interval [a, b] (the
+// closed-form bounds of spec(K)), coefficients, the smallest value of p_d on
+// the exact discrete spectrum of an N^3 grid (N = 0: not checked), and the
+// factored form (empty when the factorisation fails its check).
+struct ChebSetup {
+    double a = 0, b = 0, pmin = 0, g = 1, sign = 1;
+    std::vector<double> coef;
+    std::vector<evc_ctx::ChebFactor> fac;
+};
+
+const char* cheb_setup(int order, double h, int d, double c, int N, ChebSetup& out)
+{
+    if (order != 2 && order != 4) return "stencil order must be 2 or 4";
+    if (!(h > 0.0) || !std::isfinite(h)) return "grid spacing must be > 0";
+    if (d < 1 || d > 32) return "Chebyshev degree must be an integer in [1, 32]";
+    if (!(c > 0.0) || !std::isfinite(c)) return "kinetic shift c must be > 0";
+    out.a = c;
+    out.b = c + (order == 2 ? 6.0 : 8.0) / (h * h);
+    out.coef.assign(d + 1, 0.0);
+    evc::cheb_coefficients(d, out.a, out.b, out.coef.data());
+    // T = M^2 is SPD iff p_d > 0 on the spectrum of K: the periodic
+    // stencil's eigenvalues are c + sum over axes of the axis symbol at
+    // theta = 2 pi k / N.
+    out.pmin = 1e300;
+    if (N > 0) {
+        std::vector<double> sym(N);
+        for (int k = 0; k < N; ++k) sym[k] = axis_symbol(order, h, 2.0 * M_PI * k / N);
+        std::sort(sym.begin(), sym.end());
+        sym.erase(std::unique(sym.begin(), sym.end()), sym.end());
+        for (size_t i1 = 0; i1 < sym.size(); ++i1)
+            for (size_t i2 = i1; i2 < sym.size(); ++i2)
+                for (size_t i3 = i2; i3 < sym.size(); ++i3)
+                    out.pmin = std::min(out.pmin, cheb_eval(out.coef, out.a, out.b,
+                                                            out.a + sym[i1] + sym[i2] + sym[i3]));
+    }
+    if (!cheb_factor(out.coef, out.a, out.b, out.fac, out.g, out.sign)) out.fac.clear();
+    return nullptr;
+}
+
+}  // namespace
+
+namespace {
+
 // ------------------------------------------------------- step sequence
 
 cudaEvent_t pool_event(evc_ctx* ctx)
@@ -1156,6 +1200,27 @@ extern "C" {
 
 int evc_version(void) { return 10000; }
 
+int evc_cheb_kinetic(int order, double h, int degree, double c, int N, double* info,
+                     double* coef, double* factors, int* nfac)
+{
+    if (!info || !coef || !factors || !nfac || N < 0) return EVC_EINVAL;
+    ChebSetup cs;
+    if (cheb_setup(order, h, degree, c, N, cs)) return EVC_EINVAL;
+    info[0] = cs.a;
+    info[1] = cs.b;
+    info[2] = N > 0 ? cs.pmin : 0.0;
+    info[3] = cs.g;
+    info[4] = cs.sign;
+    for (int j = 0; j <= degree; ++j) coef[j] = cs.coef[j];
+    *nfac = (int)cs.fac.size();
+    for (size_t f = 0; f < cs.fac.size(); ++f) {
+        factors[3 * f] = cs.fac[f].re;
+        factors[3 * f + 1] = cs.fac[f].im;
+        factors[3 * f + 2] = cs.fac[f].pair ? 1.0 : 0.0;
+    }
+    return EVC_OK;
+}
+
 int evc_create_csr(const evc_csr* A, int precision, void* stream, evc_ctx** out)
 {
     if (!out) return EVC_EINVAL;
@@ -1320,38 +1385,23 @@ int evc_set_precond(evc_ctx* ctx, int kind, double param0, double param1)
         if (ctx->op != OP_STENCIL)
             return fail(ctx, EVC_EUNSUPPORTED, "the kinetic Chebyshev preconditioner needs a stencil context");
         const int d = (int)param0;
-        if ((double)d != param0 || d < 1 || d > 32)
+        if ((double)d != param0)
             return fail(ctx, EVC_EINVAL, "Chebyshev degree must be an integer in [1, 32]");
-        if (!(param1 > 0.0) || !std::isfinite(param1))
-            return fail(ctx, EVC_EINVAL, "kinetic shift c must be > 0");
         const StencilOp& s = ctx->sten;
-        const double a = param1;
-        const double b = param1 + (s.order == 2 ? 6.0 : 8.0) / (s.h * s.h);
-        std::vector<double> coef(d + 1);
-        evc::cheb_coefficients(d, a, b, coef.data());
-        // T = M^2 is SPD iff p_d > 0 on the spectrum of K: the periodic
-        // stencil's eigenvalues are c + sum over axes of the axis symbol at
-        // theta = 2 pi k / N.
-        const int N = s.N;
-        std::vector<double> sym(N);
-        for (int k = 0; k < N; ++k) sym[k] = axis_symbol(s.order, s.h, 2.0 * M_PI * k / N);
-        std::sort(sym.begin(), sym.end());
-        sym.erase(std::unique(sym.begin(), sym.end()), sym.end());
-        double pmin = 1e300;
-        for (size_t i1 = 0; i1 < sym.size(); ++i1)
-            for (size_t i2 = i1; i2 < sym.size(); ++i2)
-                for (size_t i3 = i2; i3 < sym.size(); ++i3)
-                    pmin = std::min(pmin, cheb_eval(coef, a, b, a + sym[i1] + sym[i2] + sym[i3]));
-        if (!(pmin > 0.0))
-            return fail(ctx, EVC_EINVAL, "Chebyshev preconditioner not positive on spec(K) (min %g)", pmin);
+        ChebSetup cs;
+        if (const char* why = cheb_setup(s.order, s.h, d, param1, s.N, cs))
+            return fail(ctx, EVC_EINVAL, "%s", why);
+        if (!(cs.pmin > 0.0))
+            return fail(ctx, EVC_EINVAL, "Chebyshev preconditioner not positive on spec(K) (min %g)", cs.pmin);
         ctx->prec = kind;
         ctx->cheb_degree = d;
         ctx->cheb_c = param1;
-        ctx->cheb_a = a;
-        ctx->cheb_b = b;
-        ctx->cheb_coef = coef;
-        if (!cheb_factor(coef, a, b, ctx->cheb_fac, ctx->cheb_g, ctx->cheb_sign))
-            ctx->cheb_fac.clear();   // Clenshaw's recurrence only
+        ctx->cheb_a = cs.a;
+        ctx->cheb_b = cs.b;
+        ctx->cheb_coef = cs.coef;
+        ctx->cheb_fac = cs.fac;          // empty: Clenshaw's recurrence only
+        ctx->cheb_g = cs.g;
+        ctx->cheb_sign = cs.sign;
     } else {
         return fail(ctx, EVC_EINVAL, "unknown preconditioner kind %d", kind);
     }

@@ -49,7 +49,7 @@ EXPORTED = [
     "evc_get_profile", "evc_autotune", "evc_server_create", "evc_server_add_matrix", "evc_server_submit",
     "evc_server_poll", "evc_server_wait", "evc_server_stats", "evc_server_destroy",
     "evc_gauss_quadrature_static", "evc_wait_selftest", "evc_last_error", "evc_destroy",
-    "evc_version",
+    "evc_version", "evc_cheb_kinetic",
 ]
 
 
@@ -136,6 +136,8 @@ def load(path: str | None = None):
             "evc_last_error": (C.c_char_p, [vp]),
             "evc_destroy": (None, [vp]),
             "evc_version": (i32, []),
+            "evc_cheb_kinetic": (i32, [i32, d, i32, d, i32, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double), ip]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -367,6 +369,23 @@ def evc_destroy(ctx):
 
 def evc_version():
     return int(load().evc_version())
+
+
+def evc_cheb_kinetic(order, h, degree, c=1.0, N=0):
+    """The kinetic Chebyshev preconditioner the library builds (host only):
+    dict with a, b, pmin (over the N^3 grid's spectrum; 0.0 for N = 0), g,
+    sign, coef[d+1] and factors [(re, im, is_pair)]."""
+    lib = load()
+    info = (C.c_double * 5)()
+    coef = (C.c_double * (max(degree, 0) + 1))()
+    fac = (C.c_double * (3 * max(degree, 1)))()
+    nf = C.c_int(0)
+    rc = lib.evc_cheb_kinetic(order, h, degree, c, N, info, coef, fac, C.byref(nf))
+    if rc != EVC_OK:
+        raise EvcError(rc, "evc_cheb_kinetic: invalid arguments")
+    return {"a": info[0], "b": info[1], "pmin": info[2], "g": info[3], "sign": info[4],
+            "coef": np.array(coef[:degree + 1]),
+            "factors": [(fac[3 * f], fac[3 * f + 1], fac[3 * f + 2] != 0.0) for f in range(nf.value)]}
 
 
 # ------------------------------------------------------------- convenience
