@@ -147,6 +147,18 @@ def _roofline(evc, recs, peak, peak_kind, stencil_name="stencil_pass_kernel"):
     if best is None:
         return None, per_kind
     name, t, b, cnt = best
+    if name in ("finish", "reduce", "init"):
+        # per-column FP64 scalar work (eigensolves, reductions): chains of
+        # dependent operations, bound by their latency, not by a bandwidth
+        kernel = {"finish": "quad_kernel", "reduce": "reorth_reduce_kernel"}.get(name, name)
+        roof = {"bound": "latency", "kernel": kernel, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launches": cnt, "ms_per_launch_avg": t / cnt,
+                "share_of_step": None,
+                "note": "small problem: the dominant class is FP64 per-column work bound by its "
+                        "dependency chains; no bandwidth roofline applies"}
+        tot = sum(v["ms"] for v in per_kind.values())
+        roof["share_of_step"] = round(t / tot, 3) if tot > 0 else None
+        return roof, per_kind
     kernel = {"stencil": stencil_name, "csr": "csr_pass_kernel",
               "dots": "reorth_dots_kernel", "update": "reorth_update_kernel"}.get(name, name)
     ach = b / (t * 1e-3) / 1e9
