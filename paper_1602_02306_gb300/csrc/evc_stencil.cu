@@ -287,7 +287,8 @@ constexpr int PTW = 8;     // patch-variant block tile width (points along x)
 // block of 220 KB.  13-point (R = 2): as many as let two blocks share an SM
 // (113 KB each) -- measured 23% faster than a deeper pipeline with one block --
 // falling back to the one-block rule when not even one plane allows that.  For
-// R = 1 the two rules measured within 1%, the one-block rule ahead.
+// R = 1 the one-block rule measured 1% ahead on one stream and 4% ahead with
+// four concurrent chunk groups (52.3 against 54.3 ms per 64^3 count).
 template <int R, int MASK, int PX, int PY>
 __host__ __device__ constexpr int patch_depth()
 {
