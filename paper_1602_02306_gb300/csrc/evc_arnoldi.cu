@@ -182,15 +182,11 @@ cudaError_t launch_arnoldi_quad(const Run& r, int i, cudaStream_t st)
 {
     if (i > kArnoldiMaxSteps) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(3 * i * i + i) * sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        const size_t mx = (size_t)(3 * kArnoldiMaxSteps * kArnoldiMaxSteps + kArnoldiMaxSteps) *
-                          sizeof(double);
-        cudaError_t e = cudaFuncSetAttribute(arnoldi_quad_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const size_t mx = (size_t)(3 * kArnoldiMaxSteps * kArnoldiMaxSteps + kArnoldiMaxSteps) *
+                      sizeof(double);
+    const cudaError_t e = smem_limit_once(attr, arnoldi_quad_kernel, mx);
+    if (e != cudaSuccess) return e;
     arnoldi_quad_kernel<<<r.ncol_real, AQT, smem, st>>>(r, i);
     return cudaGetLastError();
 }

@@ -13,10 +13,28 @@
 // extra pass over the vectors.  Per-column scalars are stored [step][column].
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace evc {
+
+// Raise a kernel's dynamic shared-memory limit on the current device, once per
+// process and device: `done` is that kernel's bitmask of devices already set.
+// Launches from several host threads (the request server's slots) may both
+// set it the first time, which is harmless; the mask itself is atomic.
+template <typename F>
+inline cudaError_t smem_limit_once(std::atomic<uint64_t>& done, F* kernel, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev >= 0 && dev < 64 ? (uint64_t)1 << dev : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 constexpr int CW = 32;                 // columns per chunk
 constexpr int kMaxSteps = 256;         // == EVC_MAX_STEPS

@@ -700,12 +700,9 @@ size_t update_smem(int i)
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(reorth_dots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)dots_smem<T>(kMaxSteps));
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = smem_limit_once(attr, reorth_dots_kernel<T>, dots_smem<T>(kMaxSteps));
+    if (e != cudaSuccess) return e;
     reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), DTHREADS, dots_smem<T>(i), st>>>(r, i);
     return cudaGetLastError();
 }
@@ -726,12 +723,9 @@ cudaError_t launch_coef(const Run& r, int i, cudaStream_t st)
 template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(reorth_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)update_smem<T>(kMaxSteps));
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = smem_limit_once(attr, reorth_update_kernel<T>, update_smem<T>(kMaxSteps));
+    if (e != cudaSuccess) return e;
     reorth_update_kernel<T><<<dim3(r.nblk, r.nchunk), UTHREADS, update_smem<T>(i), st>>>(r, i);
     return cudaGetLastError();
 }
@@ -746,11 +740,9 @@ cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st)
     while (qb < 32 && qb * 2 * 152 <= r.ncol_real) qb <<= 1;
     while (qb > 1 && (size_t)qb * 3 * kk * sizeof(double) > 96 * 1024) qb >>= 1;
     const size_t smem = (size_t)qb * 3 * kk * sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t ea = smem_limit_once(attr, quad_kernel, 96 * 1024);
+    if (ea != cudaSuccess) return ea;
     if (r.arnoldi) {
         const cudaError_t e = launch_arnoldi_quad(r, i, st);
         if (e != cudaSuccess) return e;

@@ -506,12 +506,9 @@ void launch_patch(dim3 grid, cudaStream_t st, const KArgs& a)
     constexpr int STP = patch_threads<R>();
     constexpr size_t smem =
         (size_t)(patch_depth<R, MASK, PX, PY>() + 1) * (NB + PX * PY * (1 + NOP)) * STP * 16;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(stencil_patch_kernel<T, R, MASK, PX, PY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    // a failure here shows as the launch's error
+    static std::atomic<uint64_t> attr{0};
+    smem_limit_once(attr, stencil_patch_kernel<T, R, MASK, PX, PY>, smem);
     stencil_patch_kernel<T, R, MASK, PX, PY><<<grid, STP, smem, st>>>(a);
 }
 
@@ -544,12 +541,8 @@ template <typename T, int R, bool JAC, int MASK>
 void launch_one(dim3 grid, cudaStream_t st, const KArgs& a)
 {
     constexpr size_t smem = (size_t)(DEPTH + 1) * stencil_loads<R, MASK>() * STH * 16;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(stencil_pass_kernel<T, R, JAC, MASK>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_limit_once(attr, stencil_pass_kernel<T, R, JAC, MASK>, smem);
     stencil_pass_kernel<T, R, JAC, MASK><<<grid, STH, smem, st>>>(a);
 }
 
