@@ -102,3 +102,18 @@ def test_binding_structs_match_the_c_layout(tmp_path):
             assert getattr(cls, field).offset == int(val), (name, field)
         seen += 1
     assert seen > 30
+
+
+def test_missing_library_fails_loudly():
+    # no CPU fallback: without libevc.so every entry point raises
+    import subprocess
+    import sys
+    code = ("from paper_1602_02306_gb300 import evc\n"
+            "try:\n"
+            "    evc.load('/nonexistent/libevc.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    raise SystemExit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 3 and "not built" in r.stdout
