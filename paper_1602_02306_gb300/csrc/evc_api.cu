@@ -1041,6 +1041,7 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
         if (!(ctx->gexec && k == ctx->gkey)) {
             drop_graph(ctx);
             cudaGraph_t g = nullptr;
+            NvtxRange nv("evc: capture the count's graph");
             CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
             rc = enqueue();
             cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
@@ -1058,8 +1059,10 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
             }
             ctx->gkey = k;
         }
+        NvtxRange nv("evc: launch the count's graph");
         CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
     } else {
+        NvtxRange nv("evc: enqueue the count (no graph)");
         rc = enqueue();
         if (rc) return rc;
     }
@@ -1374,6 +1377,7 @@ int evc_set_values(evc_ctx* ctx, const void* values, int on_device)
 int evc_set_precond(evc_ctx* ctx, int kind, double param0, double param1)
 {
     if (!ctx) return EVC_EINVAL;
+    NvtxRange nv("evc: set the preconditioner");
     if (kind == EVC_PREC_IDENTITY) {
         ctx->prec = kind;
     } else if (kind == EVC_PREC_JACOBI) {
@@ -1660,6 +1664,7 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec)
 int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning* out)
 {
     if (!ctx || nshift < 1 || nprobe < 1 || maxsteps < 1) return EVC_EINVAL;
+    NvtxRange nv("evc: autotune");
     // short counts of the caller's shape (placeholder shifts: the timing of
     // a fixed number of steps does not depend on them)
     const int kt = std::min(maxsteps, 6);

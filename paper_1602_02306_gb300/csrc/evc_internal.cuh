@@ -16,8 +16,19 @@
 #include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace evc {
+
+// A named NVTX range over a host-side phase (graph capture, replay, set-up,
+// autotuning, a server batch), visible to Nsight tools; without an attached
+// tool the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Raise a kernel's dynamic shared-memory limit on the current device, once per
 // process and device: `done` is that kernel's bitmask of devices already set.

@@ -152,6 +152,7 @@ void schedule(evc_server* s)
 
 void run_batch(evc_server* s, Slot* sl, Batch* b)
 {
+    evc::NvtxRange nv("evc: server batch");
     Req* head = b->reqs.front();
     evc_ctx* c;
     {
