@@ -17,7 +17,7 @@ paper's steps in the paper's order:
   with the same counter-hashed Rademacher probes and the same stop rule as the
   Lanczos oracle.
 
-Parity unpinned parts: none -- the pins are in tests/test_oracle_pins.py
+Parity unpinned parts: none -- the pins are in tests/test_oracle_arnoldi_pins.py
 (Arnoldi = Lanczos for T = I and symmetric A; exact count from exhaustive
 Sylvester-Hadamard probes at k = n; exactness at p distinct eigenvalues).
 """

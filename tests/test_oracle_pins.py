@@ -126,6 +126,27 @@ def test_jacobi_preconditioner_definition():
 
 
 @pytest.mark.parametrize("order", [2, 4])
+def test_stencil_jacobi_uses_the_operator_diagonal(order):
+    # The Jacobi scaling of a stencil operator must use the diagonal of the
+    # operator itself: a_rr = e_r^T A e_r, assembled here through apply_A on
+    # unit vectors (apply_A is pinned to the plane-wave symbols above), so a
+    # wrong kinetic diagonal in the Jacobi set-up (a 7-point value for the
+    # 13-point stencil, a missing V, a wrong 1/h^2) fails.  M is diagonal.
+    N, h, tau, eps = 5, 0.3, -1.25, 1e-3
+    V = I.gaussian_wells(N, h, nwells=3, seed=1)
+    P = O.Problem.stencil(N, h, order, V, O.PREC_JACOBI, jac_eps=eps)
+    n = N ** 3
+    for r in (0, 7, 62, n - 1):
+        e = np.zeros(n)
+        e[r] = 1.0
+        a_rr = O.apply_A(P, e)[r]
+        Me = O.apply_M(P, tau, e)
+        want = 1.0 / np.sqrt(abs(a_rr - tau) + eps)
+        assert abs(Me[r] - want) <= 1e-14 * want
+        assert np.count_nonzero(Me) == 1
+
+
+@pytest.mark.parametrize("order", [2, 4])
 def test_chebyshev_coefficients_match_numpy_interpolant(order):
     # numpy's Chebyshev.interpolate uses first-kind Chebyshev points: the same
     # interpolant of x^-1/2, computed by an independent library.
