@@ -265,7 +265,7 @@ def run_ours(args):
         sname = "stencil_patch_kernel"
     roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname)
     # ---- e2e: host V (pinned) -> device, count, per-probe results -> host
-    Vh = torch.from_numpy(W.potential().astype(np.float32)).pin_memory() if W.kind == "stencil" else None
+    Vh = torch.from_numpy(W.potential()).pin_memory() if W.kind == "stencil" else None
     evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
     t_e2e = None
     if not args.skip_e2e:
@@ -279,7 +279,7 @@ def run_ours(args):
             evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
         t_e2e = time.perf_counter() - t0
         barrier()
-    h2d = W.n * 4 if Vh is not None else 0
+    h2d = W.n * 8 if Vh is not None else 0
     d2h = S * m * 8 + S * 8 + S * 4
     # ---- accuracy trial: the same count with the basis rounded to BF16 when stored
     L_bf16 = None

@@ -54,7 +54,13 @@ typedef enum {
  *              preconditioner applies in float32; alpha, beta, the
  *              reorthogonalisation coefficients, the tridiagonal eigensolve
  *              and the quadrature weights in float64 (dot products accumulate
- *              short float32 runs and sum them in float64).                 */
+ *              short float32 runs and sum them in float64).  CSR contexts:
+ *              the diagonal of A is kept in float64 as given, and per shift
+ *              the diagonal of the shifted operator, (a_rr - tau) m_r^2 with
+ *              Jacobi or a_rr - tau, and the Jacobi scales m_r are formed from
+ *              it in float64 and rounded once; the stored diagonal entries do
+ *              not enter the float32 row sums.  A Jacobi scale formed from a
+ *              rounded a_rr would carry its error magnified by up to 1/eps.  */
 enum { EVC_FP64 = 0, EVC_MIXED = 1 };
 
 /* Preconditioners T = M^2 (Sec. 6; all SPD, so C keeps the inertia of
@@ -115,9 +121,12 @@ int evc_create_stencil(int N, double h, int order, const void* V, int V_is_fp32,
                        int on_device, int precision, void* stream, evc_ctx** out);
 
 /* Replace the matrix values without changing the structure: V (stencil
- * context, N^3 values) or the CSR values (nnz values), with the type given
- * at creation.  Host (on_device = 0) or device pointer; copied into the
- * context's own device buffer on its stream.                                  */
+ * context, N^3 values) or the CSR values (nnz values), in the type given at
+ * creation (val_is_fp32 / V_is_fp32).  Host (on_device = 0) or device
+ * pointer; copied (converted to the context's type when it differs) into the
+ * context's own device buffer on its stream; a CSR context re-forms its
+ * float64 diagonal from the values as given.  EVC_EINVAL when the context
+ * borrowed its values at creation.                                           */
 int evc_set_values(evc_ctx* ctx, const void* values, int on_device);
 
 /* Choose the preconditioner (see the EVC_PREC_* list above).                */
@@ -419,10 +428,17 @@ void evc_server_destroy(evc_server* srv);
  *   d_alpha : double[k * ncol],     d_alpha[t*ncol + c] = alpha_{t+1}
  *   d_beta  : double[(k+1) * ncol], d_beta[t*ncol + c]  = beta_{t+1} (t >= 1 used)
  *   d_kcol  : int32[ncol] per-column sizes 1 <= kc <= k, or NULL for k
- *   vnorm2  : ||v||^2 (n for the library's Rademacher probes)
+ *   vnorm2  : ||v||^2 (n for the library's Rademacher probes), finite, >= 0
  *   d_quad  : double[ncol] output
- * All pointers are device pointers; the call only enqueues one kernel on
- * `stream` (NULL = legacy default stream) and returns.
+ *   d_status: int32[1] output, or NULL: set to EVC_OK on the stream before the
+ *             kernel runs, then to the first failure the kernel meets --
+ *             EVC_EINVAL for a d_kcol entry outside [1, k] (that column is
+ *             not computed) or EVC_ENUMERIC for an eigensolve that did not
+ *             converge (non-finite input); such columns get NaN in d_quad.
+ * All pointers are device pointers; the call only enqueues a 4-byte memset
+ * of d_status (when given) and one kernel on `stream` (NULL = legacy default
+ * stream) and returns, so d_status is meaningful once the stream has reached
+ * that point (synchronise, or order later work after it).
  * Limits: 1 <= k <= EVC_MAX_STEPS, ncol >= 1, k * ncol <= EVC_STATIC_QUAD_MAX;
  * larger requests return EVC_EINVAL without launching anything, with a
  * message in errbuf (optional host buffer of errlen bytes).
@@ -435,8 +451,8 @@ void evc_server_destroy(evc_server* srv);
  * give wrong results -- serialise them.                                       */
 #define EVC_STATIC_QUAD_MAX 262144
 int evc_gauss_quadrature_static(const double* d_alpha, const double* d_beta, const int* d_kcol,
-                                int k, int ncol, double vnorm2, double* d_quad, void* stream,
-                                char* errbuf, size_t errlen);
+                                int k, int ncol, double vnorm2, double* d_quad, int* d_status,
+                                void* stream, char* errbuf, size_t errlen);
 
 /* evc_wait_selftest -- checks the failure detection of the streaming kernels
  * without making the GPU fault or hang.  Every device-side wait of the library

@@ -61,6 +61,7 @@ struct evc_ctx {
     // stencil
     StencilOp sten{};
     void* own_V = nullptr;
+    int val_fp32 = 0;             // type of the values given at creation (1: float32)
     // preconditioner
     int prec = EVC_PREC_IDENTITY;
     double jac_eps = 1e-3;
@@ -200,6 +201,7 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     void* w = uses_work(c) ? take(3 * (size_t)nchunk * vec) : nullptr;
     if (work) *work = w;
     r.jac = uses_jac(c) ? take((size_t)S * c->n * c->tsize) : nullptr;
+    r.dsh = c->op == OP_CSR ? take((size_t)S * c->n * c->tsize) : nullptr;
     auto D = [&](size_t cnt) { return reinterpret_cast<double*>(take(cnt * 8)); };
     auto I = [&](size_t cnt) { return reinterpret_cast<int*>(take(cnt * 4)); };
     r.sigma = D(ncol);
@@ -275,16 +277,28 @@ __global__ void csr_diag_kernel(const int64_t* rp, const int32_t* col, const voi
     }
 }
 
+// Copy `count` matrix values (float32 when src_fp32, else float64; host or
+// device) into dst in the context's type.  With diag set (CSR contexts), also
+// form the FP64 diagonal from the values as given, before any rounding to the
+// context's type: the Jacobi scaling and the shifted diagonal derive from it.
 int upload_values(evc_ctx* ctx, void* dst, const void* src, int64_t count, int src_fp32,
-                  int on_device)
+                  int on_device, double* diag = nullptr)
 {
     const size_t ssz = src_fp32 ? 4 : 8;
     const bool same = (src_fp32 ? 4u : 8u) == ctx->tsize;
+    const int dblocks = (int)std::min<int64_t>((ctx->n + 255) / 256, 152 * 16);
+    auto form_diag = [&](const void* vals) -> int {
+        if (!diag) return EVC_OK;
+        csr_diag_kernel<<<dblocks, 256, 0, ctx->stream>>>(ctx->csr.row_ptr, ctx->csr.col, vals,
+                                                          src_fp32, diag, ctx->n);
+        CU(cudaGetLastError());
+        return EVC_OK;
+    };
     if (same) {
         CU(cudaMemcpyAsync(dst, src, count * ssz, on_device ? cudaMemcpyDeviceToDevice
                                                             : cudaMemcpyHostToDevice,
                            ctx->stream));
-        return EVC_OK;
+        return form_diag(dst);
     }
     const void* dsrc = src;
     void* tmp = nullptr;
@@ -293,6 +307,8 @@ int upload_values(evc_ctx* ctx, void* dst, const void* src, int64_t count, int s
         CU(cudaMemcpyAsync(tmp, src, count * ssz, cudaMemcpyHostToDevice, ctx->stream));
         dsrc = tmp;
     }
+    int rc = form_diag(dsrc);
+    if (rc) return rc;
     const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
     if (ctx->tsize == 4)
         convert_kernel<float, double><<<blocks, 256, 0, ctx->stream>>>(
@@ -790,7 +806,8 @@ int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
     const int64_t vstride = r.n * CW;
     int rc;
     if (ctx->op == OP_CSR) {
-        const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1);
+        const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
+                             (double)r.S * r.n * sizeof(T);
         const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk;
         rc = rec(ctx, EVC_K_CSR, i, fixed, per,
                  [&] { return launch_csr_pass<T>(ctx->csr, r, i, false, st); });
@@ -833,12 +850,14 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
     const double colb = (double)r.ncol * 8;
     int rc = rec(ctx, EVC_K_INIT, 0, colb * 8, 0.0, [&] { return launch_init_state(r, st); });
     if (!rc) rc = rec(ctx, EVC_K_INIT, 0, 0.0, vchunk, [&] { return launch_init_probe<T>(r, st); });
-    if (!rc && uses_jac(ctx)) {
+    if (!rc && (uses_jac(ctx) || ctx->op == OP_CSR)) {
+        // Jacobi scales and (CSR) the shifted operator's diagonal, per shift
         const double vdiag = ctx->op == OP_STENCIL ? ctx->sten.cd : 0.0;
-        rc = rec(ctx, EVC_K_JACOBI, 0, (double)r.S * r.n * sizeof(T) + r.n * 8.0, 0.0, [&] {
+        const double outs = (r.jac ? 1.0 : 0.0) + (r.dsh ? 1.0 : 0.0);
+        rc = rec(ctx, EVC_K_JACOBI, 0, outs * r.S * r.n * sizeof(T) + r.n * 8.0, 0.0, [&] {
             return launch_jacobi_scales<T>(r, ctx->op == OP_CSR ? ctx->csr.diag : nullptr,
                                            ctx->op == OP_STENCIL ? ctx->sten.V : nullptr, vdiag,
-                                           ctx->jac_eps, st);
+                                           ctx->jac_eps, uses_jac(ctx) && !r.arnoldi, st);
         });
     }
     if (rc) return rc;
@@ -855,7 +874,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             // the CSR structure and values once; per chunk, one gathered 32-column
             // x row per stored entry, the output and q_{i-1}
             const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
-                                 (uses_jac(ctx) ? (double)r.S * r.n * sizeof(T) : 0.0);
+                                 (uses_jac(ctx) ? 2.0 : 1.0) * r.S * r.n * sizeof(T);
             const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk * (1 + (qprev ? 1 : 0));
             rc = rec(ctx, EVC_K_CSR, i, fixed, per,
                      [&] { return launch_csr_pass<T>(ctx->csr, r, i, uses_jac(ctx), st); });
@@ -1172,6 +1191,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->n = src->n;
     c->csr = src->csr;
     c->nnz = src->nnz;
+    c->val_fp32 = src->val_fp32;
     c->sten = src->sten;
     c->prec = src->prec;
     c->jac_eps = src->jac_eps;
@@ -1265,23 +1285,26 @@ int evc_create_csr(const evc_csr* A, int precision, void* stream, evc_ctx** out)
         ctx->csr.row_ptr = static_cast<const int64_t*>(ctx->own_rowptr);
         ctx->csr.col = static_cast<const int32_t*>(ctx->own_col);
     }
+    ctx->csr.n = n;
+    ctx->csr.nnz = nnz;
+    ctx->val_fp32 = A->val_is_fp32 ? 1 : 0;
+    if (dmalloc(reinterpret_cast<void**>(&ctx->own_diag), n * 8)) return cleanup(EVC_ENOMEM);
+    ctx->csr.diag = ctx->own_diag;
+    // the FP64 diagonal comes from the values as given (float64 input stays
+    // float64 there even when the context stores float32 values)
     const bool same = (A->val_is_fp32 ? 4u : 8u) == ctx->tsize;
     if (A->on_device && same) {
         ctx->csr.val = A->val;
+        csr_diag_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, ctx->stream>>>(
+            ctx->csr.row_ptr, ctx->csr.col, A->val, A->val_is_fp32, ctx->own_diag, n);
+        if (cudaGetLastError() != cudaSuccess) return cleanup(EVC_ECUDA);
     } else {
         if (dmalloc(&ctx->own_val, nnz * ctx->tsize)) return cleanup(EVC_ENOMEM);
-        rc = upload_values(ctx, ctx->own_val, A->val, nnz, A->val_is_fp32, A->on_device);
+        rc = upload_values(ctx, ctx->own_val, A->val, nnz, A->val_is_fp32, A->on_device,
+                           ctx->own_diag);
         if (rc) return cleanup(rc);
         ctx->csr.val = ctx->own_val;
     }
-    ctx->csr.n = n;
-    ctx->csr.nnz = nnz;
-    if (dmalloc(reinterpret_cast<void**>(&ctx->own_diag), n * 8)) return cleanup(EVC_ENOMEM);
-    csr_diag_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, ctx->stream>>>(
-        ctx->csr.row_ptr, ctx->csr.col, A->on_device ? A->val : ctx->csr.val,
-        A->on_device ? A->val_is_fp32 : (ctx->tsize == 4), ctx->own_diag, n);
-    if (cudaGetLastError() != cudaSuccess) return cleanup(EVC_ECUDA);
-    ctx->csr.diag = ctx->own_diag;
     // visit order of the rows: by decreasing length, so the rows that share a
     // warp in the operator kernel have similar lengths
     {
@@ -1344,6 +1367,7 @@ int evc_create_stencil(int N, double h, int order, const void* V, int V_is_fp32,
             evc_destroy(ctx);
             return EVC_ENOMEM;
         }
+        ctx->val_fp32 = V_is_fp32 ? 1 : 0;
         int rc = upload_values(ctx, ctx->own_V, V, ctx->n, V_is_fp32, on_device);
         if (rc == EVC_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = EVC_ECUDA;
         if (rc) {
@@ -1362,16 +1386,9 @@ int evc_set_values(evc_ctx* ctx, const void* values, int on_device)
     void* dst = ctx->op == OP_STENCIL ? ctx->own_V : ctx->own_val;
     if (!dst) return fail(ctx, EVC_EINVAL, "values were borrowed at creation; update them in place");
     const int64_t cnt = ctx->op == OP_STENCIL ? ctx->n : ctx->nnz;
-    const int fp32 = ctx->tsize == 4;
-    int rc = upload_values(ctx, dst, values, cnt, fp32, on_device);
-    if (rc) return rc;
-    if (ctx->op == OP_CSR) {
-        csr_diag_kernel<<<(int)std::min<int64_t>((ctx->n + 255) / 256, 152 * 16), 256, 0,
-                          ctx->stream>>>(ctx->csr.row_ptr, ctx->csr.col, ctx->csr.val, fp32,
-                                         ctx->own_diag, ctx->n);
-        CU(cudaGetLastError());
-    }
-    return EVC_OK;
+    // the values come in the type given at creation
+    return upload_values(ctx, dst, values, cnt, ctx->val_fp32, on_device,
+                         ctx->op == OP_CSR ? ctx->own_diag : nullptr);
 }
 
 int evc_set_precond(evc_ctx* ctx, int kind, double param0, double param1)

@@ -3,6 +3,12 @@
 // line of the loop body), with M = I or the Jacobi scaling
 // M = diag((|a_rr - sigma| + eps)^(-1/2)) fused as row and column scales.
 //
+// Row r of C x is  m_r sum_{j != r} a_rj m_j x_j  +  d_r x_r  with the
+// diagonal d_r = (a_rr - sigma) m_r^2 (or a_rr - sigma without M) taken from
+// a per-shift array formed in FP64: the stored diagonal entries are skipped in
+// the row sum, so in FP32 the shift never cancels against a_rr, and a rounded
+// a_rr never reaches m_r^2, which magnifies it by up to 1/eps.
+//
 // Every gathered x row of a chunk is one contiguous 128-byte (FP32) / 256-byte
 // (FP64) segment; q_i = s_i P_i is scaled on the fly.
 #include "evc_internal.cuh"
@@ -20,9 +26,9 @@ struct CArgs {
     int64_t chunk_stride;
     const double* insc;     // s_i per column
     const double* ppc;      // beta_i s_{i-1} per column
-    const double* sigma;
     const int* shift_of;
     const void* jac;
+    const void* dsh;        // T[S][n] diagonal of the shifted (scaled) operator
     const int* chunk_active;
 };
 
@@ -83,7 +89,7 @@ csr_pass_kernel(CArgs a)
         T myval = 0;
         if (k0 + sub < len) {
             mycol = __ldg(a.op.col + kk);
-            myval = __ldg(val + kk);
+            myval = mycol == (int)row ? (T)0 : __ldg(val + kk);   // diagonal: from dsh
         }
         const int cnt = (int)min((int64_t)LPR, mx - k0);
         int t = 0;
@@ -118,15 +124,14 @@ csr_pass_kernel(CArgs a)
     const T* pp = a.pp ? static_cast<const T*>(a.pp) + ch * a.chunk_stride : nullptr;
     Pack<T> prev;
     if (pp) prev = ldg16(pp + row * CW + sub * W);
+    const T* dsh = static_cast<const T*>(a.dsh);
     Pack<T> res;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         const int c = c0 + w;
-        T center = cen.v[w];
-        T mr = 1;
-        if (JAC) { mr = __ldg(jr[w] + row); center *= mr; }
-        T r = acc[w] - (T)a.sigma[c] * center;
-        if (JAC) r *= mr;
+        T r = acc[w];
+        if (JAC) r *= __ldg(jr[w] + row);
+        r += __ldg(dsh + (int64_t)a.shift_of[c] * n + row) * cen.v[w];
         r *= (T)a.insc[c];
         if (pp) r -= (T)a.ppc[c] * prev.v[w];
         res.v[w] = r;
@@ -153,9 +158,9 @@ cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, c
     a.chunk_stride = r.chunk_stride;
     a.insc = r.scl + (int64_t)(i - 1) * r.ncol;
     a.ppc = r.ppc;
-    a.sigma = r.sigma;
     a.shift_of = r.shift_of;
     a.jac = r.jac;
+    a.dsh = r.dsh;
     a.chunk_active = r.chunk_active;
     constexpr int RPW = 32 / (CW / (16 / (int)sizeof(T)));
     const int nt = op.threads > 0 ? op.threads : kThreads;

@@ -94,6 +94,9 @@ struct Run {
     double* gram;            // [kmax(kmax+1)/2][ncol]  G_ab = q_a . q_b, a >= b
     double* part_nrm;        // [nchunk][nblk][CW]
     void* jac;               // T[S][n]  (Jacobi scales, when used)
+    void* dsh;               // T[S][n]  CSR contexts: the diagonal of the shifted operator,
+                             //   (a_rr - sigma) m_r^2 (Lanczos with Jacobi) or a_rr - sigma,
+                             //   formed in FP64 from the FP64 diagonal, then rounded
     // device scalars, rewritten before each replay
     uint64_t* seed;          // [1]
     double* tol;             // [1]
@@ -177,7 +180,7 @@ template <typename T>
 cudaError_t launch_init_probe(const Run& r, cudaStream_t st);
 template <typename T>
 cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V, double vdiag,
-                                 double eps, cudaStream_t st);
+                                 double eps, bool jac_form, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st);
 template <typename T>

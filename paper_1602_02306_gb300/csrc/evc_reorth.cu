@@ -96,17 +96,26 @@ __global__ void init_state_kernel(Run r)
 }
 
 template <typename T>
-__global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, double vdiag, double eps)
+__global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, double vdiag, double eps,
+                                    int jac_form)
 {
-    // M = diag((|a_rr - tau| + eps)^(-1/2)) per shift
+    // M = diag((|a_rr - tau| + eps)^(-1/2)) per shift, and (CSR) the diagonal
+    // of the shifted operator: (a_rr - tau) m_r^2 when M scales it, else
+    // a_rr - tau.  Both from the FP64 diagonal, rounded once at the end: near
+    // a_rr = tau, m_r^2 = 1/(|a_rr - tau| + eps) amplifies an error in a_rr
+    // by up to 1/eps, so neither may be formed from rounded values.
     const int64_t total = (int64_t)r.S * r.n;
     T* jac = static_cast<T*>(r.jac);
+    T* dsh = static_cast<T*>(r.dsh);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(e / r.n);
         const int64_t row = e % r.n;
         const double d = diag ? diag[row] : (double)V[row] + vdiag;
-        jac[e] = (T)(1.0 / sqrt(fabs(d - r.shifts[s]) + eps));
+        const double x = d - r.shifts[s];
+        const double m2 = 1.0 / (fabs(x) + eps);
+        if (jac) jac[e] = (T)sqrt(m2);
+        if (dsh) dsh[e] = (T)(jac_form ? x * m2 : x);
     }
 }
 
@@ -674,12 +683,12 @@ cudaError_t launch_init_probe(const Run& r, cudaStream_t st)
 
 template <typename T>
 cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V, double vdiag,
-                                 double eps, cudaStream_t st)
+                                 double eps, bool jac_form, cudaStream_t st)
 {
     const int64_t total = (int64_t)r.S * r.n;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
     jacobi_scale_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(r, diag, static_cast<const T*>(V),
-                                                             vdiag, eps);
+                                                             vdiag, eps, jac_form ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -762,9 +771,9 @@ cudaError_t launch_active(const Run& r, int i, cudaStream_t st)
 template cudaError_t launch_init_probe<float>(const Run&, cudaStream_t);
 template cudaError_t launch_init_probe<double>(const Run&, cudaStream_t);
 template cudaError_t launch_jacobi_scales<float>(const Run&, const double*, const void*, double,
-                                                 double, cudaStream_t);
+                                                 double, bool, cudaStream_t);
 template cudaError_t launch_jacobi_scales<double>(const Run&, const double*, const void*, double,
-                                                  double, cudaStream_t);
+                                                  double, bool, cudaStream_t);
 template cudaError_t launch_dots<float>(const Run&, int, cudaStream_t);
 template cudaError_t launch_dots<double>(const Run&, int, cudaStream_t);
 template cudaError_t launch_update<float>(const Run&, int, cudaStream_t);

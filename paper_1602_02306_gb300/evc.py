@@ -131,8 +131,8 @@ def load(path: str | None = None):
             "evc_server_wait": (i32, [vp, C.c_int64, d, C.POINTER(evc_result)]),
             "evc_server_stats": (i32, [vp, C.POINTER(evc_server_counters)]),
             "evc_server_destroy": (None, [vp]),
-            "evc_gauss_quadrature_static": (i32, [vp, vp, vp, i32, i32, d, vp, vp, C.c_char_p,
-                                                  C.c_size_t]),
+            "evc_gauss_quadrature_static": (i32, [vp, vp, vp, i32, i32, d, vp, vp, vp,
+                                                  C.c_char_p, C.c_size_t]),
             "evc_last_error": (C.c_char_p, [vp]),
             "evc_destroy": (None, [vp]),
             "evc_version": (i32, []),
@@ -350,11 +350,14 @@ def evc_server_destroy(srv):
         load().evc_server_destroy(srv)
 
 
-def evc_gauss_quadrature_static(d_alpha, d_beta, d_kcol, k, ncol, vnorm2, d_quad, stream=None):
-    """Allocation-free quadrature (device pointers in and out); returns (status, message)."""
+def evc_gauss_quadrature_static(d_alpha, d_beta, d_kcol, k, ncol, vnorm2, d_quad, d_status=None,
+                                stream=None):
+    """Allocation-free quadrature (device pointers in and out; d_status an
+    optional device int32 that receives the kernel's status); returns
+    (status of the call, message)."""
     buf = C.create_string_buffer(256)
     rc = load().evc_gauss_quadrature_static(d_alpha, d_beta, d_kcol, int(k), int(ncol),
-                                            float(vnorm2), d_quad, stream, buf, 256)
+                                            float(vnorm2), d_quad, d_status, stream, buf, 256)
     return rc, buf.value.decode()
 
 
