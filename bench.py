@@ -2,13 +2,19 @@
 estimator on one GB300, FP32-mixed (headline) and FP64, with the HBM
 roofline of the dominant kernel and the FP64 CPU oracle timed beside it.
 
-Workload (default): FD Hamiltonian H = -1/2 Lap_h + V, 7-point periodic 64^3
-(n = 262,144), h = 0.3, 32 Gaussian wells; shifts lambda_min - 1 and eta;
-Chebyshev degree-8 kinetic preconditioner; 64 Rademacher probes per shift;
-30 Lanczos steps.  One benchmark step = one full count (2 shifts x 64 probes x
-30 Lanczos steps, every kernel of the path) with the matrix resident in HBM.
+Workload (default, the largest single-GPU configuration): a generic sparse
+symmetric indefinite matrix, n = 2,000,000, power-law row lengths (mean ~30,
+at most ~2000), N(0,1) values, diagonal U(-5, 5); interval [-0.5, 0.5];
+Jacobi preconditioner 1/(|a_ii - sigma| + 1e-3); 128 Rademacher probes per
+shift; 50 Lanczos steps.  One benchmark step = one full count (2 shifts x 128
+probes x 50 Lanczos steps, every kernel of the path) with the matrix resident
+in HBM.  The same line carries the other workloads of the path under
+`extra_workloads` (the 64^3 FD Hamiltonian with the Chebyshev kinetic
+preconditioner, and 32-shift spectrum slicing of the 13-point 96^3
+Hamiltonian with early stop), each with its own time and roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--extras a,b]
 
 Multi-GPU (torchrun): the path shards by probe columns with no data
 exchange; every rank runs its own replica on its own probes (seed + rank)
@@ -98,7 +104,7 @@ _METHOD = [0]        # EVC_METHOD_LANCZOS; --method arnoldi sets 1
 _SHAPES = {"patch": 0, "zb": 0, "groups": 0, "csr_threads": 0}   # 0: library default
 
 
-def _make_ctx(evc, W, precision, stream_ptr, V=None):
+def _make_ctx(evc, W, precision, stream_ptr, V=None, nshift=None):
     if W.kind == "stencil":
         ctx = evc.Context.stencil(W.N, W.h, W.order, W.potential() if V is None else V,
                                   precision=precision, stream=stream_ptr)
@@ -121,11 +127,11 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None):
             evc.evc_set_option(ctx.h, evc.EVC_OPT_STENCIL_ZB, _SHAPES["zb"])
         if _SHAPES["groups"]:
             evc.evc_set_option(ctx.h, evc.EVC_OPT_STENCIL_GROUPS, _SHAPES["groups"])
-    ctx.reserve(len(W.shifts), W.nprobe, W.maxsteps)
+    ctx.reserve(len(W.shifts) if nshift is None else nshift, W.nprobe, W.maxsteps)
     return ctx
 
 
-def _roofline(evc, recs, peak, peak_kind, stencil_name="stencil_pass_kernel"):
+def _roofline(evc, recs, peak, peak_kind, stencil_name="stencil_pass_kernel", W=None):
     """Roofline of the kernel class with the largest device time in the launch
     list: achieved = sum of its launches' algorithmic bytes / sum of their
     CUDA-event durations.  Launches that ran as concurrent chunk groups are
@@ -168,28 +174,237 @@ def _roofline(evc, recs, peak, peak_kind, stencil_name="stencil_pass_kernel"):
             "launches": cnt, "share_of_step": None}
     tot = sum(v["ms"] for v in per_kind.values())
     roof["share_of_step"] = round(t / tot, 3) if tot > 0 else None
-    _attach_traffic(roof)
+    _attach_traffic(roof, W)
     return roof, per_kind
 
 
-def _attach_traffic(roof):
-    """DRAM traffic of one launch of the dominant kernel from the committed ncu
-    capture, only while the kernel's source is unchanged since the capture."""
+def _function_text(src, name):
+    """Text of the definition of function (or `struct X`) `name` in src, with
+    whitespace collapsed: from the name to the end of its brace-delimited body."""
+    import re
+    if name.startswith("struct "):
+        pats = [r"\bstruct\s+" + re.escape(name.split()[1]) + r"\s*\{"]
+    else:
+        pats = [r"\b" + re.escape(name) + r"\s*\("]
+    for mt in re.finditer(pats[0], src):
+        j = mt.end() - 1
+        if src[j] == "(":
+            depth = 0
+            while j < len(src):
+                depth += {"(": 1, ")": -1}.get(src[j], 0)
+                if depth == 0:
+                    break
+                j += 1
+            j += 1
+            while j < len(src) and src[j] in " \t\n":
+                j += 1
+            if j >= len(src) or src[j] != "{":
+                continue            # a call or a declaration, not the definition
+        depth, e = 0, j
+        while e < len(src):
+            depth += {"{": 1, "}": -1}.get(src[e], 0)
+            if depth == 0:
+                break
+            e += 1
+        # the declaration lines just above the name (template parameters,
+        # __global__ / __launch_bounds__ qualifiers), up to a blank line, a
+        # comment or the end of the previous statement
+        st = src.rfind("\n", 0, mt.start()) + 1
+        for _ in range(3):
+            prev = src.rfind("\n", 0, st - 1) + 1 if st > 0 else 0
+            line = src[prev:st].strip()
+            if st == 0 or not line or line.startswith("//") or line.endswith((";", "}", "*/")):
+                break
+            st = prev
+        return " ".join(src[st:e + 1].split())
+    raise KeyError(f"no definition of {name}")
+
+
+def _device_code_sha(spec):
+    """sha256 over the device code a kernel runs: spec = [[file, [function or
+    'struct X' names]], ...], each definition's text in the listed order."""
     import hashlib
-    rec = {"stencil_pass_kernel": "profiles/stencil_pass_fd64_traffic.json",
-           "stencil_patch_kernel": "profiles/stencil_patch_fd64_traffic.json"}.get(roof["kernel"])
-    if not rec or not os.path.exists(os.path.join(ROOT, rec)):
+    h = hashlib.sha256()
+    for rel, names in spec:
+        src = open(os.path.join(ROOT, rel)).read()
+        for nm in names:
+            h.update(_function_text(src, nm).encode())
+    return h.hexdigest()
+
+
+def _attach_traffic(roof, W=None):
+    """DRAM traffic of one launch of the dominant kernel from the committed ncu
+    capture (profiles/<kernel>_<workload>_traffic.json), attached only while the
+    device code of that kernel -- its definition and every device function and
+    argument struct it uses, hashed as text -- is unchanged since the capture."""
+    if W is None:
         return
-    d = json.load(open(os.path.join(ROOT, rec)))
-    src = os.path.join(ROOT, d["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d["source_sha256"]:
+    rec = os.path.join(ROOT, "profiles", f"{roof['kernel']}_{W.name}_traffic.json")
+    if not os.path.exists(rec):
+        roof["traffic_note"] = "no ncu capture of this kernel on this workload"
         return
-    roof["traffic"] = d["dram_bytes"]
+    d = json.load(open(rec))
+    try:
+        sha = _device_code_sha(d["device_code"])
+    except (KeyError, OSError) as e:
+        roof["traffic_note"] = f"device code of the capture not found: {e}"
+        return
+    if sha != d["device_code_sha256"]:
+        roof["traffic_note"] = "device code changed since the ncu capture"
+        return
+    per_unit = d["dram_bytes"] / d["algorithmic_bytes"]
+    # the capture's launch may be smaller than the bench's; DRAM bytes scale with
+    # the algorithmic bytes of the launch (same kernel, same shape per chunk)
+    roof["traffic"] = per_unit * roof["bytes_per_launch_avg"]
+    roof["traffic_per_algorithmic_byte"] = round(per_unit, 4)
     roof["traffic_launch"] = d["launch"]
-    roof["traffic_launch_algorithmic_bytes"] = d["algorithmic_bytes"]
     roof["traffic_source"] = d["profile"]
     if "note" in d:
         roof["traffic_note"] = d["note"]
+
+
+def _measure(evc, W, args, stream, peak, peak_kind, steps, warmup, seed, tune=True):
+    """Time `steps` counts of W on a mixed context with the matrix resident
+    (after `warmup` untimed counts), then one profiled count for the per-kernel
+    device times.  Returns the open context and the measurements."""
+    import torch
+    S, m, k = len(W.shifts), W.nprobe, W.maxsteps
+    ctx = _make_ctx(evc, W, evc.EVC_MIXED, stream.cuda_stream)
+    ws = evc.evc_workspace_bytes(ctx.h, S, m, k)
+    # the library's autotuner picks the tile shapes for this launch shape
+    # (short counts, before and outside the timed region)
+    tuning = ctx.autotune(S, m, k) if tune and not args.no_autotune else None
+    dq = torch.empty(S * m, dtype=torch.float64, device="cuda")
+    dL = torch.empty(S, dtype=torch.float64, device="cuda")
+    ds = torch.empty(S, dtype=torch.int32, device="cuda")
+
+    def timed(nsteps, nwarm, profile):
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 1 if profile else 0)
+        for _ in range(nwarm):
+            evc.evc_count_slices_async(ctx.h, W.shifts, m, k, W.tol, seed, dL.data_ptr(),
+                                       dq.data_ptr(), ds.data_ptr())
+        evc.evc_sync(ctx.h)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        _barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nsteps):
+            evc.evc_count_slices_async(ctx.h, W.shifts, m, k, W.tol, seed, dL.data_ptr(),
+                                       dq.data_ptr(), ds.data_ptr())
+        e1.record(stream)
+        evc.evc_sync(ctx.h)
+        torch.cuda.synchronize()
+        _barrier()
+        return e0.elapsed_time(e1), dL.cpu().numpy(), ds.cpu().numpy(), dq.cpu().numpy()
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms, L, st, q = timed(steps, warmup, profile=False)
+    clk = clocks.stop()
+    # per-kernel device times: one more count of the same workload, replayed
+    # with a pair of timing events around every kernel, or around each step's
+    # stencil segment when its chunk groups run concurrently (kept out of the
+    # timed region above, whose events see only the whole counts)
+    timed(1, 0, profile=True)
+    recs = evc.evc_get_profile(ctx.h)
+    evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
+    launches = sum(1 for r in recs if not r[4])   # span records are not launches
+    # the stencil class runs the patch kernel when the tuner chose 2 x 2 patches
+    # (passes without Jacobi scaling, N even)
+    sname = "stencil_pass_kernel"
+    patch = tuning.get("stencil_patch") if tuning else _SHAPES["patch"]
+    if W.kind == "stencil" and patch == 2 and W.precond != "jacobi" and W.N % 2 == 0:
+        sname = "stencil_patch_kernel"
+    roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname, W)
+    psteps = float(m * int(np.sum(st)))
+    return ctx, {"ms": ms, "L": L, "steps_used": st, "quad": q, "clocks": clk, "roofline": roof,
+                 "kernels": per_kind, "launches": launches, "psteps": psteps, "ws": ws,
+                 "tuning": tuning}
+
+
+_WORLD = [1]
+
+
+def _barrier():
+    if _WORLD[0] > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _fp64_leg(evc, W, args, stream, seed, ws_mixed, shifts=None):
+    """The FP64 path on the same workload (or a subset of its shifts), timed."""
+    import torch
+    torch.cuda.empty_cache()
+    shifts = list(W.shifts) if shifts is None else list(shifts)
+    S, m, k = len(shifts), W.nprobe, W.maxsteps
+    free, _ = torch.cuda.mem_get_info()
+    need = 2 * ws_mixed * S / len(W.shifts)
+    if need > 0.9 * free:
+        return None, f"FP64 workspace {need / 1e9:.0f} GB does not fit next to the rest"
+    ctx = _make_ctx(evc, W, evc.EVC_FP64, stream.cuda_stream, nshift=S)
+    if not args.no_autotune:
+        ctx.autotune(S, m, k)
+    nsteps = max(1, args.steps // 2)
+    for _ in range(1):
+        L, q, st = ctx.count_slices(shifts, m, k, tol=W.tol, seed=seed)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nsteps):
+        L, q, st = ctx.count_slices(shifts, m, k, tol=W.tol, seed=seed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    ctx.close()
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms, "psteps": float(m * int(np.sum(st))), "L": L, "steps_used": st,
+            "quad": q}, None
+
+
+def _extra(evc, name, args, stream, peak, peak_kind, seed):
+    """Another workload of the path, measured the same way, for the same line."""
+    import torch
+    from paper_1602_02306_gb300 import workloads
+    W = workloads.WORKLOADS[name]()
+    torch.cuda.empty_cache()
+    ctx, r = _measure(evc, W, args, stream, peak, peak_kind, args.extra_steps, 1, seed)
+    ctx.close()
+    out = {"workload": W.name, "n": W.n, "shifts": len(W.shifts), "probes_per_shift": W.nprobe,
+           "lanczos_steps_max": W.maxsteps, "tol": W.tol,
+           "steps_used": [int(x) for x in r["steps_used"]],
+           "value": round(r["psteps"] / (r["ms"] / args.extra_steps * 1e-3), 1), "unit": UNIT,
+           "ms_per_step": round(r["ms"] / args.extra_steps, 3), "steps": args.extra_steps,
+           "roofline": r["roofline"], "kernels": r["kernels"], "clocks": r["clocks"],
+           "tiles": r["tuning"], "gpu_launches_per_step": r["launches"]}
+    if name == "slicing96" and not args.skip_fp64:
+        # the FP64 basis of all 32 shifts does not fit beside anything; every
+        # shift's columns (and its stop rule) are independent of the others, so
+        # FP64 runs on three of the shifts and each is compared with the same
+        # shift of the mixed run
+        sub = [0, 15, 31]
+        f64, note = _fp64_leg(evc, W, args, stream, seed, r["ws"], shifts=[W.shifts[s] for s in sub])
+        if f64 is None:
+            out["fp64_subset"] = {"skipped": note}
+        else:
+            out["fp64_subset"] = {
+                "shifts": sub, "n_below_fp64": [round(float(x), 4) for x in f64["L"]],
+                "n_below_mixed": [round(float(r["L"][s]), 4) for s in sub],
+                "mixed_minus_fp64": [float(r["L"][s] - f64["L"][j]) for j, s in enumerate(sub)],
+                "steps_fp64": [int(x) for x in f64["steps_used"]],
+                "steps_mixed": [int(r["steps_used"][s]) for s in sub],
+                "value_fp64": round(f64["psteps"] / (f64["ms_per_step"] * 1e-3), 1)}
+    elif W.kind == "stencil" and not args.skip_fp64:
+        f64, note = _fp64_leg(evc, W, args, stream, seed, r["ws"])
+        if f64 is not None:
+            out["fp64"] = {"value": round(f64["psteps"] / (f64["ms_per_step"] * 1e-3), 1),
+                           "ms_per_step": round(f64["ms_per_step"], 3)}
+            est_m = float(r["L"][-1] - r["L"][0])
+            est_f = float(f64["L"][-1] - f64["L"][0])
+            out["estimate"] = {"mixed": est_m, "fp64": est_f, "mixed_minus_fp64": est_m - est_f}
+    return out
 
 
 def run_ours(args):
@@ -200,6 +415,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    _WORLD[0] = world
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -209,103 +425,45 @@ def run_ours(args):
     seed = args.seed + rank
     peak, peak_kind = _peaks()
     stream = torch.cuda.Stream()
-    sp = stream.cuda_stream
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def timed(ctx, steps, warmup, profile):
-        evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 1 if profile else 0)
-        dq = torch.empty(S * m, dtype=torch.float64, device="cuda")
-        dL = torch.empty(S, dtype=torch.float64, device="cuda")
-        ds = torch.empty(S, dtype=torch.int32, device="cuda")
-        for _ in range(warmup):
-            evc.evc_count_slices_async(ctx.h, W.shifts, m, k, W.tol, seed, dL.data_ptr(),
-                                       dq.data_ptr(), ds.data_ptr())
-        evc.evc_sync(ctx.h)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(steps):
-            evc.evc_count_slices_async(ctx.h, W.shifts, m, k, W.tol, seed, dL.data_ptr(),
-                                       dq.data_ptr(), ds.data_ptr())
-        e1.record(stream)
-        evc.evc_sync(ctx.h)
-        torch.cuda.synchronize()
-        barrier()
-        ms = e0.elapsed_time(e1)
-        return ms, dL.cpu().numpy(), ds.cpu().numpy()
 
     # ---- headline: FP32-mixed, inputs resident
-    ctx = _make_ctx(evc, W, evc.EVC_MIXED, sp)
-    ws_mixed = evc.evc_workspace_bytes(ctx.h, S, m, k)
-    # the library's autotuner picks the tile shapes for this launch shape
-    # (short counts, before and outside the timed region)
-    tuning = None if args.no_autotune else ctx.autotune(S, m, k)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms_mixed, L_mixed, steps_mixed = timed(ctx, args.steps, args.warmup, profile=False)
-    clk = clocks.stop()
-    # per-kernel device times: one more count of the same workload, replayed
-    # with a pair of timing events around every kernel, or around each step's
-    # stencil segment when its chunk groups run concurrently (kept out of the
-    # timed region above, whose events see only the whole counts)
-    timed(ctx, 1, 0, profile=True)
-    recs = evc.evc_get_profile(ctx.h)
-    launches_per_step = sum(1 for r in recs if not r[4])   # span records are not launches
-    # the stencil class runs the patch kernel when the tuner chose 2 x 2 patches
-    # (passes without Jacobi scaling, N even)
-    sname = "stencil_pass_kernel"
-    patch = tuning.get("stencil_patch") if tuning else _SHAPES["patch"]
-    if W.kind == "stencil" and patch == 2 and W.precond != "jacobi" and W.N % 2 == 0:
-        sname = "stencil_patch_kernel"
-    roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname)
-    # ---- e2e: host V (pinned) -> device, count, per-probe results -> host
-    Vh = torch.from_numpy(W.potential()).pin_memory() if W.kind == "stencil" else None
-    evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
+    ctx, r = _measure(evc, W, args, stream, peak, peak_kind, args.steps, args.warmup, seed)
+    ms_mixed, L_mixed, steps_mixed = r["ms"], r["L"], r["steps_used"]
+    # ---- e2e: the step's inputs from pinned host memory (V of a stencil
+    # context, the CSR values otherwise, in the type they were given in),
+    # count, per-probe results back to the host
+    if W.kind == "stencil":
+        hv = W.potential()
+    else:
+        hv = W.csr()[2]
+    Vh = torch.from_numpy(np.ascontiguousarray(hv)).pin_memory()
     t_e2e = None
     if not args.skip_e2e:
         evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
         torch.cuda.synchronize()
-        barrier()
+        _barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            if Vh is not None:
-                evc.evc_set_values(ctx.h, Vh.data_ptr(), False)
+            evc.evc_set_values(ctx.h, Vh.data_ptr(), False)
             evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
         t_e2e = time.perf_counter() - t0
-        barrier()
-    h2d = W.n * 8 if Vh is not None else 0
+        _barrier()
+    h2d = int(Vh.numel() * Vh.element_size())
     d2h = S * m * 8 + S * 8 + S * 4
+    del Vh
     # ---- accuracy trial: the same count with the basis rounded to BF16 when stored
     L_bf16 = None
     if not args.skip_bf16:
         evc.evc_set_option(ctx.h, evc.EVC_OPT_BASIS_BF16, 1)
-        _, L_bf16, _ = timed(ctx, 1, 0, profile=False)
+        L_bf16, _, _ = ctx.count_slices(W.shifts, m, k, tol=W.tol, seed=seed)
         evc.evc_set_option(ctx.h, evc.EVC_OPT_BASIS_BF16, 0)
     ctx.close()
     torch.cuda.empty_cache()
     # ---- FP64 path on the same GPU
-    ms_fp64, L_fp64, fp64_note = None, None, None
-    if not args.skip_fp64:
-        free, _ = torch.cuda.mem_get_info()
-        need = 2 * ws_mixed
-        if need > 0.9 * free:
-            fp64_note = f"FP64 workspace {need / 1e9:.0f} GB does not fit next to the rest"
-        else:
-            ctx64 = _make_ctx(evc, W, evc.EVC_FP64, sp)
-            if not args.no_autotune:
-                ctx64.autotune(S, m, k)
-            ms_fp64, L_fp64, steps_fp64 = timed(ctx64, max(1, args.steps // 2), 1, profile=False)
-            psteps64 = float(m * int(np.sum(steps_fp64)))
-            ctx64.close()
+    f64, fp64_note = (None, "--skip-fp64") if args.skip_fp64 else \
+        _fp64_leg(evc, W, args, stream, seed, r["ws"])
 
-    # probe-steps per count: every probe of a shift runs that shift's steps
-    psteps = float(m * int(np.sum(steps_mixed)))
+    psteps = r["psteps"]
     t_step = ms_mixed / args.steps
     t_max = t_step
     e2e_t = (t_e2e / args.steps) if t_e2e is not None else float("nan")
@@ -315,8 +473,7 @@ def run_ours(args):
         t_max, e2e_t = float(t[0]), float(t[1])
     value = world * psteps / (t_max * 1e-3)
     est_mixed = float(L_mixed[-1] - L_mixed[0])
-    est_fp64 = float(L_fp64[-1] - L_fp64[0]) if L_fp64 is not None else None
-    fp64_steps = max(1, args.steps // 2)
+    est_fp64 = float(f64["L"][-1] - f64["L"][0]) if f64 is not None else None
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max, 3),
@@ -328,26 +485,31 @@ def run_ours(args):
                    "precond": {"cheb": f"chebyshev-{int(W.prec_params[0])} kinetic (c={W.prec_params[1]}), "
                                        f"{['factored', 'clenshaw'][_CHEB_FORM[0]]}",
                                "jacobi": "jacobi (eps 1e-3)", "identity": "none"}[W.precond],
-                   "precision": "FP32 vectors/operator, FP64 alpha/beta/reorth coefficients/eig",
+                   "precision": "FP32 vectors/operator, FP64 alpha/beta/reorth coefficients/eig"
+                                + (", FP64 diagonal and Jacobi set-up" if W.kind == "csr" else ""),
                    "step": "one full count: all shifts x probes x executed Lanczos steps",
-                   "l2": f"inputs larger than L2 (Lanczos basis {ws_mixed / 1e9:.1f} GB workspace streamed every step)",
+                   "l2": f"inputs larger than L2 (Lanczos basis {r['ws'] / 1e9:.1f} GB workspace "
+                         f"streamed every step)",
                    "parallelism": f"replicas{world}",
                    "method": ["lanczos (Algorithms 1-2)", "arnoldi (Sec. 4, Algorithm 3)"][_METHOD[0]],
-                   "tiles": tuning if tuning is not None else "defaults (--no-autotune)"},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk,
-        "roofline": roof,
-        "kernels": per_kind,
+                   "tiles": r["tuning"] if r["tuning"] is not None else "defaults (--no-autotune)"},
+        "gpu_launches": r["launches"] * args.steps,
+        "clocks": r["clocks"],
+        "roofline": r["roofline"],
+        "kernels": r["kernels"],
         "e2e": {"value": round(world * psteps / e2e_t, 1) if t_e2e is not None else None, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "evc_set_values(V from pinned host) + evc_count_slices (host outputs)"},
-        "fp64": {"skipped": fp64_note or "--skip-fp64"} if ms_fp64 is None else {
-            "value": round(world * psteps64 / (ms_fp64 / fp64_steps * 1e-3), 1), "unit": UNIT,
-            "ms_per_step": round(ms_fp64 / fp64_steps, 3)},
+                "path": ("evc_set_values(V" if W.kind == "stencil" else "evc_set_values(CSR values")
+                        + " float64 from pinned host) + evc_count_slices (host outputs)"},
+        "fp64": {"skipped": fp64_note} if f64 is None else {
+            "value": round(world * f64["psteps"] / (f64["ms_per_step"] * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(f64["ms_per_step"], 3)},
         "estimate": {"mixed": est_mixed, "fp64": est_fp64,
                      "mixed_minus_fp64": (est_mixed - est_fp64) if est_fp64 is not None else None,
                      "n_below_mixed": [round(float(x), 4) for x in L_mixed],
-                     "n_below_fp64": None if L_fp64 is None else [round(float(x), 4) for x in L_fp64]},
+                     "n_below_fp64": None if f64 is None else [round(float(x), 4) for x in f64["L"]],
+                     "max_abs_per_probe_mixed_minus_fp64": None if f64 is None else
+                     float(np.max(np.abs(r["quad"] - f64["quad"].reshape(-1))))},
         "bf16_basis": None if L_bf16 is None else {
             "estimate": float(L_bf16[-1] - L_bf16[0]),
             "minus_fp64": (float(L_bf16[-1] - L_bf16[0]) - est_fp64) if est_fp64 is not None else None,
@@ -358,6 +520,11 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_probes, seed=args.seed)
+    # ---- the other workloads of the path, each with its own time and roofline
+    if rank == 0 and world == 1 and args.extras:
+        line["extra_workloads"] = {}
+        for name in [x for x in args.extras.split(",") if x and x != args.workload]:
+            line["extra_workloads"][name] = _extra(evc, name, args, stream, peak, peak_kind, seed)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -496,6 +663,62 @@ def run_serving(args):
         print(json.dumps(line), flush=True)
 
 
+def run_laplace_family(args):
+    """The paper's Laplace mesh family (Sec. 7; Table 1 "Laplace", Table 2's
+    h = 2^-6 .. 2^-10): estimate against k for the unpreconditioned Lanczos
+    estimator (scalar Jacobi), m = 50, tau = 3000, mixed precision, next to the
+    closed-form count -- the mesh dependence of k that the paper's
+    preconditioners remove.  One JSON line."""
+    import torch
+    from paper_1602_02306_gb300 import evc, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    evc.load()
+    ks = [int(x) for x in args.family_k.split(",")]
+    rows = []
+    t_all = time.perf_counter()
+    tot_ps, tot_ms = 0.0, 0.0
+    for e in range(6, 11):
+        W = workloads.laplace_paper(e, k=max(ks))
+        exact = workloads.laplace_exact_below(e)
+        stream = torch.cuda.Stream()
+        ctx = _make_ctx(evc, W, evc.EVC_MIXED, stream.cuda_stream)
+        row = {"h": f"2^-{e}", "n": W.n, "exact": exact, "k": {}}
+        first5 = None
+        for k in ks:
+            kk = min(k, W.n)
+            ctx.count_slices(W.shifts, W.nprobe, kk, seed=args.seed)   # graph capture, untimed
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            L, q, st = ctx.count_slices(W.shifts, W.nprobe, kk, seed=args.seed)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            se = float(q[0].std(ddof=1) / np.sqrt(W.nprobe))
+            rel = abs(float(L[0]) - exact) / exact
+            row["k"][kk] = {"estimate": round(float(L[0]), 2), "se": round(se, 2),
+                            "rel_err": round(rel, 4), "ms": round(ms, 2)}
+            if first5 is None and rel <= 0.05:
+                first5 = kk
+            tot_ps += W.nprobe * int(st[0])
+            tot_ms += ms
+        row["smallest_k_within_5pct"] = first5
+        rows.append(row)
+        ctx.close()
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": round(tot_ps / (tot_ms * 1e-3), 1), "unit": UNIT,
+            "n_gpus": 1, "steps": len(ks) * 5, "warmup": 1,
+            "ms_per_step": round(tot_ms / (len(ks) * 5), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "laplace2d_family_h2^-6..2^-10_tau3000_m50",
+                       "precond": "jacobi (a scalar here: the paper's unpreconditioned row)",
+                       "k_grid": ks, "step": "one count at one (h, k)"},
+            "paper": {"table1_laplace_h2^-7": {"exact": 226, "k": 134, "estimate": 232}},
+            "family": rows, "wall_s": round(time.perf_counter() - t_all, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -505,10 +728,10 @@ def run_reference(args):
     from paper_1602_02306_gb300 import workloads
     W = workloads.WORKLOADS[args.workload]()
     for _ in range(args.warmup):
-        cpu_baseline(W, args.cpu_probes, seed=args.seed)
+        cpu_baseline(W, args.ref_probes, seed=args.seed)
     times, vals = [], []
     for _ in range(args.steps):
-        cb = cpu_baseline(W, args.cpu_probes, seed=args.seed)
+        cb = cpu_baseline(W, args.ref_probes, seed=args.seed)
         times.append(cb["seconds"])
         vals.append(cb["value"])
     value = float(np.median(vals))
@@ -534,9 +757,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fd64")
+    ap.add_argument("--workload", default="powerlaw2m")
+    ap.add_argument("--extras", default="fd64,slicing96",
+                    help="other workloads measured for the same line (comma list, '' for none)")
+    ap.add_argument("--extra-steps", type=int, default=3, help="timed counts per extra workload")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-probes", type=int, default=8)
+    ap.add_argument("--family-k", default="25,50,100,134,200,256",
+                    help="laplace-family workload: the Lanczos step counts of the study")
+    ap.add_argument("--cpu-probes", type=int, default=6,
+                    help="probes per shift of the oracle's bounded sample (cpu_baseline)")
+    ap.add_argument("--ref-probes", type=int, default=2,
+                    help="probes per shift of each step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison leg")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg")
@@ -567,6 +798,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "laplace-family":
+        run_laplace_family(args)
     else:
         run_ours(args)
 

@@ -360,7 +360,10 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
  * The oldest request is never overtaken; one that cannot fit even with
  * nothing running fails with EVC_ENOMEM.  Each request's result equals the
  * result of the same request run alone (columns are independent and every
- * reduction has a batch-independent order).
+ * reduction has a batch-independent order).  A launch flags a numeric
+ * failure (EVC_ENUMERIC) once for all its columns, so a merged batch that
+ * fails is run again request by request: only the request whose own columns
+ * fail reports it.
  * ------------------------------------------------------------------------ */
 typedef struct evc_server evc_server;
 

@@ -83,6 +83,11 @@ arnoldi_quad_kernel(Run r, int i)
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    // Newton's iteration converges quadratically once every eigenvalue is
+    // scaled near +-1; one that has not met the tolerance after 100 steps (an
+    // eigenvalue of H_k close to the imaginary axis) is reported as a numeric
+    // failure instead of a quadrature from an unconverged X.
+    bool converged = false;
     for (int it = 0; it < 100; ++it) {
         for (int e = tid; e < k * k2; e += AQT) {
             const int row = e / k2, col = e % k2;
@@ -151,11 +156,14 @@ arnoldi_quad_kernel(Run r, int i)
         const double dn = block_sum(dloc, red);
         const double nn = block_sum(nloc, red);
         __syncthreads();
-        if (!(dn > 1e-28 * nn)) break;     // converged (uniform: every thread sees the same sums)
+        if (!(dn > 1e-28 * nn)) {          // converged (uniform: every thread sees the same sums)
+            converged = true;
+            break;
+        }
     }
     if (tid == 0) {
         double q = (double)r.n * 0.5 * (1.0 - X[0]);
-        if (s_bad || !isfinite(q)) {
+        if (s_bad || !converged || !isfinite(q)) {
             atomicExch(r.err, DERR_NUMERIC);
             q = 0.0;
         }

@@ -14,6 +14,7 @@
 #include "evc_internal.cuh"
 
 #include <cstring>
+#include <type_traits>
 
 namespace evc {
 namespace {
@@ -51,8 +52,10 @@ __device__ __forceinline__ Pack<T> ldg16(const T* p)
 // warp fetches 32/LPR whole x rows.  Rows are visited in the order of
 // op.perm (rows sorted by length, longest first) so the rows sharing a warp
 // have similar lengths; each group broadcasts the row's (col, val) pairs from
-// its own lanes with warp shuffles.
-template <typename T, bool JAC, int NT>
+// its own lanes with warp shuffles.  UNI: every chunk's 32 columns belong to
+// one shift (m a multiple of 32, or one shift), so a gathered entry needs one
+// Jacobi scale, not one per column.
+template <typename T, bool JAC, bool UNI, int NT>
 __global__ void __launch_bounds__(NT)
 csr_pass_kernel(CArgs a)
 {
@@ -70,9 +73,10 @@ csr_pass_kernel(CArgs a)
     const int c0 = ch * CW + sub * W;
     const T* x = static_cast<const T*>(a.x) + ch * a.chunk_stride;
     const T* val = static_cast<const T*>(a.op.val);
-    const T* jr[W];
+    constexpr int NJ = UNI ? 1 : W;             // Jacobi scale arrays in use
+    const T* jr[NJ];
 #pragma unroll
-    for (int w = 0; w < W; ++w)
+    for (int w = 0; w < NJ; ++w)
         jr[w] = JAC ? static_cast<const T*>(a.jac) + (int64_t)a.shift_of[c0 + w] * n : nullptr;
 
     const int64_t beg = valid ? a.op.row_ptr[row] : 0, end = valid ? a.op.row_ptr[row + 1] : 0;
@@ -100,10 +104,13 @@ csr_pass_kernel(CArgs a)
             const T vb = __shfl_sync(0xffffffffu, myval, grp * LPR + t + 1);
             Pack<T> xa = ldg16(x + (int64_t)ca * CW + sub * W);
             Pack<T> xb = ldg16(x + (int64_t)cb * CW + sub * W);
+            T ma = 1, mb = 1;
+            if (JAC && UNI) { ma = __ldg(jr[0] + ca); mb = __ldg(jr[0] + cb); }
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 T sa = xa.v[w], sb = xb.v[w];
-                if (JAC) { sa *= __ldg(jr[w] + ca); sb *= __ldg(jr[w] + cb); }
+                if (JAC && UNI) { sa *= ma; sb *= mb; }
+                if (JAC && !UNI) { sa *= __ldg(jr[w] + ca); sb *= __ldg(jr[w] + cb); }
                 acc[w] += va * sa + vb * sb;
             }
         }
@@ -111,10 +118,12 @@ csr_pass_kernel(CArgs a)
             const int ca = __shfl_sync(0xffffffffu, mycol, grp * LPR + t);
             const T va = __shfl_sync(0xffffffffu, myval, grp * LPR + t);
             Pack<T> xa = ldg16(x + (int64_t)ca * CW + sub * W);
+            const T ma = JAC && UNI ? __ldg(jr[0] + ca) : (T)1;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 T sa = xa.v[w];
-                if (JAC) sa *= __ldg(jr[w] + ca);
+                if (JAC && UNI) sa *= ma;
+                if (JAC && !UNI) sa *= __ldg(jr[w] + ca);
                 acc[w] += va * sa;
             }
         }
@@ -130,7 +139,7 @@ csr_pass_kernel(CArgs a)
     for (int w = 0; w < W; ++w) {
         const int c = c0 + w;
         T r = acc[w];
-        if (JAC) r *= __ldg(jr[w] + row);
+        if (JAC) r *= __ldg(jr[UNI ? 0 : w] + row);
         r += __ldg(dsh + (int64_t)a.shift_of[c] * n + row) * cen.v[w];
         r *= (T)a.insc[c];
         if (pp) r -= (T)a.ppc[c] * prev.v[w];
@@ -166,22 +175,28 @@ cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, c
     const int nt = op.threads > 0 ? op.threads : kThreads;
     const int rows_per_block = (nt / 32) * RPW;
     dim3 grid((unsigned)((op.n + rows_per_block - 1) / rows_per_block), r.nchunk);
-    switch (nt) {
-    case 128:
-        if (jacobi) csr_pass_kernel<T, true, 128><<<grid, 128, 0, st>>>(a);
-        else csr_pass_kernel<T, false, 128><<<grid, 128, 0, st>>>(a);
-        break;
-    case 256:
-        if (jacobi) csr_pass_kernel<T, true, 256><<<grid, 256, 0, st>>>(a);
-        else csr_pass_kernel<T, false, 256><<<grid, 256, 0, st>>>(a);
-        break;
-    case 512:
-        if (jacobi) csr_pass_kernel<T, true, 512><<<grid, 512, 0, st>>>(a);
-        else csr_pass_kernel<T, false, 512><<<grid, 512, 0, st>>>(a);
-        break;
-    default:
-        return cudaErrorInvalidValue;
-    }
+    // every chunk's columns share one shift when m is a multiple of 32 (the
+    // padding columns of the last chunk take the last shift) or S = 1
+    const bool uni = r.S == 1 || r.m % CW == 0;
+    auto go = [&](auto jac_t, auto uni_t, auto nt_t) {
+        csr_pass_kernel<T, decltype(jac_t)::value, decltype(uni_t)::value, decltype(nt_t)::value>
+            <<<grid, decltype(nt_t)::value, 0, st>>>(a);
+    };
+    using F = std::false_type;
+    using Tr = std::true_type;
+    auto by_nt = [&](auto jac_t, auto uni_t) -> bool {
+        switch (nt) {
+        case 128: go(jac_t, uni_t, std::integral_constant<int, 128>()); return true;
+        case 256: go(jac_t, uni_t, std::integral_constant<int, 256>()); return true;
+        case 512: go(jac_t, uni_t, std::integral_constant<int, 512>()); return true;
+        default: return false;
+        }
+    };
+    bool ok;
+    if (!jacobi) ok = by_nt(F(), F());
+    else if (uni) ok = by_nt(Tr(), Tr());
+    else ok = by_nt(Tr(), F());
+    if (!ok) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

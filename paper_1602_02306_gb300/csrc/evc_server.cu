@@ -181,6 +181,16 @@ void run_batch(evc_server* s, Slot* sl, Batch* b)
     if (rc == EVC_OK)
         rc = evc_count_slices(c, shifts.data(), 2 * R, m, head->maxsteps, head->tol, head->seed,
                               L.data(), quad.data(), steps.data());
+    // A numeric failure is flagged once for the whole launch: run each request
+    // of a merged batch alone (in the same workspace) so that only the request
+    // whose own columns fail reports it, as it would have alone.
+    std::vector<int> rcs(R, rc);
+    if (rc == EVC_ENUMERIC && R > 1) {
+        for (int q = 0; q < R; ++q)
+            rcs[q] = evc_count_slices(c, shifts.data() + 2 * q, 2, m, head->maxsteps, head->tol,
+                                      head->seed, L.data() + 2 * q, quad.data() + (size_t)2 * q * m,
+                                      steps.data() + 2 * q);
+    }
     evc_set_workspace(c, nullptr, 0);
     if (ws) {
         cudaFreeAsync(ws, st);
@@ -190,8 +200,8 @@ void run_batch(evc_server* s, Slot* sl, Batch* b)
     const double t = s->now();
     for (int q = 0; q < R; ++q) {
         Req* r = b->reqs[q];
-        r->res.status = rc;
-        if (rc == EVC_OK) {
+        r->res.status = rcs[q];
+        if (rcs[q] == EVC_OK) {
             r->res.n_below[0] = L[2 * q];
             r->res.n_below[1] = L[2 * q + 1];
             r->res.estimate = L[2 * q + 1] - L[2 * q];

@@ -119,10 +119,41 @@ def powerlaw_1m_profile() -> Workload:
                     notes={"n": 1_200_000})
 
 
+# The paper's Laplace test problem (Sec. 7, Table 1 "Laplace" row; the mesh
+# family h = 2^-6 .. 2^-10 of its mesh-independence study): the 5-point
+# Dirichlet Laplacian on the unit square scaled by 1/h^2, tau = 3000.
+LAPLACE_TAU = 3000.0
+
+
+def laplace_exact_below(e: int, tau: float = LAPLACE_TAU) -> int:
+    """n_-(A - tau I) of the h = 2^-e Laplacian from its closed-form spectrum
+    (4/h^2)(sin^2(i pi h/2) + sin^2(j pi h/2)), i, j = 1 .. 2^e - 1:
+    230, 226, 222, 220, 220 for e = 6 .. 10 (Table 1 prints 226 for e = 7)."""
+    h = 2.0 ** -e
+    i = np.arange(1, 2 ** e)
+    s = 4.0 * np.sin(i * np.pi * h / 2.0) ** 2 / h ** 2
+    return int(((s[:, None] + s[None, :]) < tau).sum())
+
+
+def laplace_paper(e: int, k: int = 134, m: int = 50) -> Workload:
+    """Laplace h = 2^-e (N = 2^e - 1 interior points per axis, n = N^2),
+    tau = 3000, m = 50 probes, k Lanczos steps (134 is Table 1's k for the
+    unpreconditioned run at h = 2^-7).  Jacobi: the diagonal is the constant
+    4/h^2, so M is a scalar and the run is the paper's unpreconditioned row."""
+    N, h = 2 ** e - 1, 2.0 ** -e
+    return Workload(name=f"laplace2d_h2^-{e}_tau3000_m{m}_k{k}", kind="csr",
+                    shifts=[LAPLACE_TAU], nprobe=m, maxsteps=k, precond="jacobi",
+                    prec_params=(1e-3, 0.0),
+                    csr_builder=lambda: I.laplace2d_dirichlet(N, scale=1.0 / h ** 2),
+                    notes={"n": N * N, "h": h, "e": e})
+
+
 WORKLOADS = {
     "fd64": fd_hamiltonian_64,
     "laplace32": laplace32,
     "slicing96": batched_slicing_96,
     "powerlaw2m": powerlaw_2m,
     "powerlaw1m": powerlaw_1m_profile,
+    "laplace2^-7": lambda: laplace_paper(7),
+    "laplace2^-10": lambda: laplace_paper(10),
 }

@@ -44,23 +44,68 @@ def test_latency_bound_class_has_no_bandwidth_roofline():
     assert roof["achieved"] is None and roof["frac"] is None and roof["peak"] is None
 
 
-def test_traffic_attached_only_while_the_source_matches(tmp_path, monkeypatch):
-    rec = json.load(open(os.path.join(ROOT, "profiles", "stencil_patch_fd64_traffic.json")))
-    roof = {"kernel": "stencil_patch_kernel", "traffic": None}
-    bench._attach_traffic(roof)
-    assert roof["traffic"] == rec["dram_bytes"]
-    assert roof["traffic_launch_algorithmic_bytes"] == rec["algorithmic_bytes"]
-    assert rec["dram_bytes"] < 1.05 * rec["algorithmic_bytes"]     # no wasted re-reads
-    # the same record against a changed source: no traffic
+class _W:
+    name = "toy_workload"
+
+
+def _fake_repo(tmp_path, body):
     fake = tmp_path / "repo"
-    shutil.copytree(os.path.join(ROOT, "profiles"), fake / "profiles")
-    src = fake / rec["source"]
-    src.parent.mkdir(parents=True)
-    src.write_text(open(os.path.join(ROOT, rec["source"])).read() + "\n// edited\n")
+    (fake / "profiles").mkdir(parents=True)
+    (fake / "k").mkdir()
+    (fake / "k" / "toy.cu").write_text(body)
+    return fake
+
+
+_SRC = """// toy kernels
+struct Args { int n; };
+
+__device__ float helper(float x) { return 2.0f * x; }
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+toy_kernel(Args a)
+{
+    if (a.n) { float y = helper(1.0f); (void)y; }
+}
+
+void host_launch(Args a) { toy_kernel<float><<<1, 1>>>(a); helper(3.0f); }
+"""
+
+
+def test_function_text_finds_definitions_not_calls():
+    t = bench._function_text(_SRC, "toy_kernel")
+    assert t.startswith("template <typename T> __global__ void __launch_bounds__(128) toy_kernel(Args a)")
+    assert t.endswith("}")
+    assert bench._function_text(_SRC, "helper").startswith("__device__ float helper(float x)")
+    assert bench._function_text(_SRC, "struct Args") == "struct Args { int n; }"
+    with pytest.raises(KeyError):
+        bench._function_text(_SRC, "missing_kernel")
+
+
+def test_traffic_attached_only_while_the_device_code_matches(tmp_path, monkeypatch):
+    fake = _fake_repo(tmp_path, _SRC)
     monkeypatch.setattr(bench, "ROOT", str(fake))
-    roof2 = {"kernel": "stencil_patch_kernel", "traffic": None}
-    bench._attach_traffic(roof2)
-    assert roof2["traffic"] is None
+    spec = [["k/toy.cu", ["struct Args", "helper", "toy_kernel"]]]
+    rec = {"kernel": "toy_kernel", "device_code": spec,
+           "device_code_sha256": bench._device_code_sha(spec),
+           "launch": "toy", "dram_bytes": 90.0, "algorithmic_bytes": 100.0, "profile": "p.md"}
+    (fake / "profiles" / "toy_kernel_toy_workload_traffic.json").write_text(json.dumps(rec))
+    roof = {"kernel": "toy_kernel", "traffic": None, "bytes_per_launch_avg": 1000.0}
+    bench._attach_traffic(roof, _W)
+    assert roof["traffic"] == pytest.approx(900.0)        # scaled to the bench's launch
+    assert roof["traffic_per_algorithmic_byte"] == pytest.approx(0.9)
+    # host code and comments around the kernel may change
+    (fake / "k" / "toy.cu").write_text(_SRC.replace("host_launch(Args a) {", "host_launch(Args a) { /* x */")
+                                       .replace("// toy kernels", "// toy kernels, edited"))
+    roof = {"kernel": "toy_kernel", "traffic": None, "bytes_per_launch_avg": 1000.0}
+    bench._attach_traffic(roof, _W)
+    assert roof["traffic"] == pytest.approx(900.0)
+    # a change in a device function the kernel calls, or in its arguments: no traffic
+    for old, new in (("2.0f * x", "3.0f * x"), ("int n;", "long n;"), ("(128)", "(256)")):
+        (fake / "k" / "toy.cu").write_text(_SRC.replace(old, new))
+        roof = {"kernel": "toy_kernel", "traffic": None, "bytes_per_launch_avg": 1000.0}
+        bench._attach_traffic(roof, _W)
+        assert roof["traffic"] is None and "changed" in roof["traffic_note"]
 
 
 class _Proc:

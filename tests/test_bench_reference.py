@@ -16,8 +16,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 @pytest.mark.slow
 def test_reference_arm_json_line():
     from paper_1602_02306_gb300 import workloads
+    # the 64^3 Hamiltonian keeps this CPU test short; the default workload
+    # (2M-row power-law CSR) runs the same code
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--cpu-probes", "4"],
+                        "--steps", "1", "--warmup", "0", "--ref-probes", "4",
+                        "--workload", "fd64"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -39,6 +42,14 @@ def test_reference_arm_json_line():
                         "d2h_bytes_per_step": 0}
     # probe-steps over the sample: 2 shifts x 4 probes x 30 steps in ms_per_step
     assert d["value"] == pytest.approx(2 * 4 * 30 / (d["ms_per_step"] / 1e3), rel=0.02)
+
+
+def test_default_workload_is_the_largest_single_gpu_config():
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert 'ap.add_argument("--workload", default="powerlaw2m")' in src
+    from paper_1602_02306_gb300 import workloads
+    W = workloads.WORKLOADS["powerlaw2m"]()
+    assert W.n == 2_000_000 and W.nprobe == 128 and W.maxsteps == 50 and len(W.shifts) == 2
 
 
 def test_reference_arm_on_other_ranks_prints_nothing():

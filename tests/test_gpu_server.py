@@ -140,3 +140,71 @@ def test_request_larger_than_budget_fails_cleanly():
         evc.evc_server_destroy(srv)
         for c in ctxs:
             c.close()
+
+
+def test_served_request_matches_the_oracle_fp64():
+    # one request through the server (merged with others) against the FP64
+    # oracle per probe, stop rule included
+    from oracle import oracle as O
+    N, h = 10, 0.3
+    V = I.gaussian_wells(N, h, nwells=4, seed=1)
+    ctx = evc.Context.stencil(N, h, 2, V, precision=evc.EVC_FP64)
+    ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+    srv = evc.evc_server_create(4 << 30, slots=1, max_batch=8)
+    try:
+        mid = evc.evc_server_add_matrix(srv, ctx.h)
+        req = dict(matrix_id=mid, xi=-2.5, eta=0.25, nprobe=24, maxsteps=25, tol=0.25, seed=5)
+        bufs = [np.zeros(48) for _ in range(4)]
+        tks = [evc.evc_server_submit(srv, **dict(req, xi=req["xi"] + 0.1 * q), quad_buf=bufs[q])
+               for q in range(4)]
+        res = [evc.evc_server_wait(srv, tk) for tk in tks]
+        P = O.Problem.stencil(N, h, 2, V, O.PREC_JACOBI, jac_eps=1e-3)
+        for q, (rc, r) in enumerate(res):
+            assert rc == evc.EVC_OK
+            qr, sr, Lr = O.count(P, [req["xi"] + 0.1 * q, req["eta"]], req["nprobe"],
+                                 req["maxsteps"], tol=req["tol"], seed=req["seed"])
+            assert list(r["steps"]) == list(sr)
+            np.testing.assert_allclose(bufs[q], qr.reshape(-1), rtol=0, atol=1e-8)
+            assert abs(r["estimate"] - (Lr[1] - Lr[0])) < 1e-9
+    finally:
+        evc.evc_server_destroy(srv)
+        ctx.close()
+
+
+def test_numeric_failure_stays_with_its_request():
+    # a shift that is finite in FP64 but overflows FP32 makes its own columns
+    # non-finite; merged with good requests, only that request fails and the
+    # others equal their results alone
+    N = 10
+    V = I.gaussian_wells(N, 0.3, nwells=4, seed=1)
+    ctx = evc.Context.stencil(N, 0.3, 2, V, precision=evc.EVC_MIXED)
+    ctx.set_precond(evc.EVC_PREC_IDENTITY)
+    Vb = I.gaussian_wells(40, 0.3, nwells=4, seed=1)
+    big = evc.Context.stencil(40, 0.3, 2, Vb, precision=evc.EVC_MIXED)
+    big.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+    srv = evc.evc_server_create(8 << 30, slots=1, max_batch=8)
+    try:
+        mid = evc.evc_server_add_matrix(srv, ctx.h)
+        mbig = evc.evc_server_add_matrix(srv, big.h)
+        good = [dict(matrix_id=mid, xi=-2.0 + 0.2 * q, eta=0.5, nprobe=32, maxsteps=15, tol=0.0,
+                     seed=9) for q in range(3)]
+        alone = []
+        for g in good:
+            rc, r = evc.evc_server_wait(srv, evc.evc_server_submit(srv, **g))
+            assert rc == evc.EVC_OK
+            alone.append(r)
+        blocker = evc.evc_server_submit(srv, mbig, -1.0, 1.0, 64, 80, 0.0, 1)
+        bad = evc.evc_server_submit(srv, mid, -1e300, 0.5, 32, 15, 0.0, 9)
+        tks = [evc.evc_server_submit(srv, **g) for g in good]
+        rc, rb = evc.evc_server_wait(srv, bad)
+        assert rc == evc.EVC_ENUMERIC
+        for tk, ra in zip(tks, alone):
+            rc, r = evc.evc_server_wait(srv, tk)
+            assert rc == evc.EVC_OK
+            assert r["estimate"] == ra["estimate"]
+        assert rb["batch_size"] > 1                      # it did share a launch
+        assert evc.evc_server_wait(srv, blocker)[0] == evc.EVC_OK
+    finally:
+        evc.evc_server_destroy(srv)
+        ctx.close()
+        big.close()

@@ -70,3 +70,24 @@ def test_random_symmetric_dense_has_exactly_the_distinct_eigenvalues():
     for lam in distinct:
         assert np.sum(np.abs(w - lam) < 1e-10) == 4
     assert np.allclose(A, A.T)
+
+
+def test_laplace_family_exact_counts():
+    # the closed-form count against a dense eigendecomposition of the assembled
+    # matrix on the small meshes, and against Table 1's printed 226 at h = 2^-7
+    import json
+    import os
+    from paper_1602_02306_gb300 import workloads as W
+    for e in (3, 4, 5):
+        h = 2.0 ** -e
+        rp, col, val = I.laplace2d_dirichlet(2 ** e - 1, scale=1.0 / h ** 2)
+        n = len(rp) - 1
+        A = np.zeros((n, n))
+        for r in range(n):
+            A[r, col[rp[r]:rp[r + 1]]] = val[rp[r]:rp[r + 1]]
+        lam = np.linalg.eigvalsh(A)
+        for tau in (100.0, 0.37 * lam.max(), 3000.0):
+            assert W.laplace_exact_below(e, tau) == int((lam < tau).sum())
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_table1_laplace.json")))
+    assert W.laplace_exact_below(7, g["tau"]) == g["exact_negative_inertia"]
+    assert [W.laplace_exact_below(e) for e in range(6, 11)] == [230, 226, 222, 220, 220]
