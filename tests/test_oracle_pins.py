@@ -464,3 +464,52 @@ def test_ga_equals_gauss_after_breakdown_and_at_k1():
     assert O.ga_quad(al, be, 30.0) == pytest.approx(O.gauss_quad(al, be, 30.0), abs=1e-9)
     al1, be1, _, _ = O.lanczos(P, 0.0, v, 1)
     assert O.ga_quad(al1, be1, 30.0) == O.gauss_quad(al1, be1, 30.0)
+
+
+# ------------------------------------------ T^{-1}-inner-product Lanczos
+
+def test_tinv_lanczos_equals_algorithm1_dense():
+    # Eq. lanT1 with y_1 = M q_1 (Sec. 4) reproduces Algorithm 1's tridiagonal
+    # for C = M (A - tau I) M, and so its Gauss quadrature
+    from oracle.lanczos_tinv import lanczos_tinv
+    n, tau, k = 60, 0.3, 14
+    A = I.random_symmetric_dense(n, seed=21)
+    rng = np.random.default_rng(22)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = (Qm * rng.uniform(0.5, 2.0, n)) @ Qm.T
+    M = 0.5 * (M + M.T)
+    T = M @ M
+    P = O.Problem.dense_matrix(A, O.PREC_DENSE, denseM=M)
+    v = O.probe_vector(0, 5, n)
+    al, be, _, kd = O.lanczos(P, tau, v, k)
+    q1 = v / np.linalg.norm(v)
+    a2, b2, k2 = lanczos_tinv(lambda x: A @ x - tau * x, lambda x: T @ x, M @ q1,
+                              np.linalg.solve(M, q1), k)
+    assert k2 == kd == k
+    np.testing.assert_allclose(a2, al, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(b2, be, rtol=1e-9, atol=1e-11)
+    assert O.gauss_quad(a2, b2, n) == pytest.approx(O.gauss_quad(al, be, n), abs=1e-9)
+    # a planted mistake -- z_1 = M q_1 instead of T^{-1} y_1 = M^{-1} q_1 --
+    # leaves alpha_1 = y_1^T (A - tau I) y_1 alone but breaks beta_2 and alpha_2
+    a3, b3, _ = lanczos_tinv(lambda x: A @ x - tau * x, lambda x: T @ x, M @ q1, M @ q1, 3)
+    assert abs(a3[0] - al[0]) < 1e-10
+    assert abs(b3[1] - be[1]) > 1e-3 * abs(be[1]) or abs(a3[1] - al[1]) > 1e-3
+
+
+def test_tinv_lanczos_equals_algorithm1_chebyshev_stencil():
+    # the kinetic Chebyshev preconditioner of the stencil oracle, T = p_8(K)^2
+    from oracle.lanczos_tinv import lanczos_tinv
+    N, h, tau, k = 4, 0.3, -1.0, 10
+    V = I.gaussian_wells(N, h, nwells=3, seed=1)
+    P = O.Problem.stencil(N, h, 2, V, O.PREC_CHEB, cheb_degree=8, cheb_c=1.0)
+    n = N ** 3
+    Mdense = np.stack([O.apply_M(P, tau, e) for e in np.eye(n)], axis=1)
+    v = O.probe_vector(1, 3, n)
+    al, be, _, kd = O.lanczos(P, tau, v, k)
+    q1 = v / np.linalg.norm(v)
+    a2, b2, k2 = lanczos_tinv(lambda x: O.apply_A(P, x) - tau * x,
+                              lambda x: O.apply_M(P, tau, O.apply_M(P, tau, x)),
+                              O.apply_M(P, tau, q1), np.linalg.solve(Mdense, q1), k)
+    assert k2 == kd
+    np.testing.assert_allclose(a2, al, rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(b2, be, rtol=1e-8, atol=1e-9)
