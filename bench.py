@@ -17,9 +17,10 @@ Hamiltonian with early stop), each with its own time and roofline.
                   [--workload NAME] [--extras a,b]
 
 Multi-GPU (torchrun): the path shards by probe columns with no data
-exchange; every rank runs its own replica on its own probes (seed + rank)
-and the job reports the sum of all ranks' probe-steps over the slowest
-rank's time ("weak" scaling).
+exchange; N ranks run one count of N x m probes per shift, rank r holding
+probe ids r*m .. (r+1)*m - 1 of the same seed, and the per-probe quadratures
+are combined on the host after the timed region.  The job reports the sum
+of all ranks' probe-steps over the slowest rank's time ("weak" scaling).
 """
 from __future__ import annotations
 
@@ -102,6 +103,8 @@ class ClockSampler:
 _CHEB_FORM = [0]     # EVC_CHEB_FACTORED; --cheb-form clenshaw sets 1
 _METHOD = [0]        # EVC_METHOD_LANCZOS; --method arnoldi sets 1
 _SHAPES = {"patch": 0, "zb": 0, "groups": 0, "csr_threads": 0}   # 0: library default
+_MAXSTEPS = [0]      # --maxsteps (profiling aid); 0 keeps the workload's own
+_PROBE_OFFSET = [0]  # under torchrun: rank * m, the rank's block of one sharded count
 
 
 def _make_ctx(evc, W, precision, stream_ptr, V=None, nshift=None):
@@ -117,6 +120,8 @@ def _make_ctx(evc, W, precision, stream_ptr, V=None, nshift=None):
     if W.precond == "cheb":
         evc.evc_set_option(ctx.h, evc.EVC_OPT_CHEB_FORM, _CHEB_FORM[0])
     evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, _METHOD[0])
+    if _PROBE_OFFSET[0]:
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_PROBE_OFFSET, _PROBE_OFFSET[0])
     if W.kind == "csr" and _SHAPES["csr_threads"]:
         evc.evc_set_option(ctx.h, evc.EVC_OPT_CSR_THREADS, _SHAPES["csr_threads"])
     if W.kind == "stencil":
@@ -321,10 +326,23 @@ def _measure(evc, W, args, stream, peak, peak_kind, steps, warmup, seed, tune=Tr
     psteps = float(m * int(np.sum(st)))
     return ctx, {"ms": ms, "L": L, "steps_used": st, "quad": q, "clocks": clk, "roofline": roof,
                  "kernels": per_kind, "launches": launches, "psteps": psteps, "ws": ws,
-                 "tuning": tuning}
+                 "tuning": tuning, "kmax": k}
 
 
 _WORLD = [1]
+
+
+def _device_time(r, steps):
+    """How much of a count the kernels fill: the per-kernel device times of the
+    profiled count against the timed counts' wall time on the device.  With
+    early stop, the launches of a step still cover stopped chunks, whose blocks
+    return at once; the gap also holds the graph's launch-to-launch gaps."""
+    busy = sum(v["ms"] for v in r["kernels"].values())
+    t = r["ms"] / steps
+    done = int(np.sum(r["steps_used"]))
+    return {"count_ms": round(t, 3), "kernels_ms": round(busy, 3),
+            "idle_ms": round(t - busy, 3), "idle_frac": round((t - busy) / t, 4),
+            "shift_steps_run": done, "shift_steps_max": len(r["steps_used"]) * int(r["kmax"])}
 
 
 def _barrier():
@@ -369,6 +387,8 @@ def _extra(evc, name, args, stream, peak, peak_kind, seed):
     import torch
     from paper_1602_02306_gb300 import workloads
     W = workloads.WORKLOADS[name]()
+    if _MAXSTEPS[0]:
+        W.maxsteps = _MAXSTEPS[0]
     torch.cuda.empty_cache()
     ctx, r = _measure(evc, W, args, stream, peak, peak_kind, args.extra_steps, 1, seed)
     ctx.close()
@@ -378,7 +398,8 @@ def _extra(evc, name, args, stream, peak, peak_kind, seed):
            "value": round(r["psteps"] / (r["ms"] / args.extra_steps * 1e-3), 1), "unit": UNIT,
            "ms_per_step": round(r["ms"] / args.extra_steps, 3), "steps": args.extra_steps,
            "roofline": r["roofline"], "kernels": r["kernels"], "clocks": r["clocks"],
-           "tiles": r["tuning"], "gpu_launches_per_step": r["launches"]}
+           "tiles": r["tuning"], "gpu_launches_per_step": r["launches"],
+           "device_time": _device_time(r, args.extra_steps)}
     if name == "slicing96" and not args.skip_fp64:
         # the FP64 basis of all 32 shifts does not fit beside anything; every
         # shift's columns (and its stop rule) are independent of the others, so
@@ -421,8 +442,14 @@ def run_ours(args):
     torch.cuda.set_device(local)
     evc.load()
     W = workloads.WORKLOADS[args.workload]()
+    if _MAXSTEPS[0]:
+        W.maxsteps = _MAXSTEPS[0]
     S, m, k = len(W.shifts), W.nprobe, W.maxsteps
-    seed = args.seed + rank
+    # N ranks run one count of N*m probes: rank r holds probe ids r*m ..
+    # (r+1)*m - 1 (same seed), and the per-probe quadratures are combined on
+    # the host after the timed region (the only exchange of the path)
+    seed = args.seed
+    _PROBE_OFFSET[0] = rank * m
     peak, peak_kind = _peaks()
     stream = torch.cuda.Stream()
 
@@ -472,6 +499,12 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max, e2e_t = float(t[0]), float(t[1])
     value = world * psteps / (t_max * 1e-3)
+    if world > 1:
+        # the sharded count's estimate over all N*m probes
+        from paper_1602_02306_gb300 import replicas
+        g = dist.new_group(backend="gloo")
+        q_all, L_all = replicas.combine(r["quad"].reshape(S, m), world * m, group=g)
+        L_mixed = L_all
     est_mixed = float(L_mixed[-1] - L_mixed[0])
     est_fp64 = float(f64["L"][-1] - f64["L"][0]) if f64 is not None else None
     line = {
@@ -490,13 +523,14 @@ def run_ours(args):
                    "step": "one full count: all shifts x probes x executed Lanczos steps",
                    "l2": f"inputs larger than L2 (Lanczos basis {r['ws'] / 1e9:.1f} GB workspace "
                          f"streamed every step)",
-                   "parallelism": f"replicas{world}",
+                   "parallelism": f"probe shards x{world}" if world > 1 else "one GPU",
                    "method": ["lanczos (Algorithms 1-2)", "arnoldi (Sec. 4, Algorithm 3)"][_METHOD[0]],
                    "tiles": r["tuning"] if r["tuning"] is not None else "defaults (--no-autotune)"},
         "gpu_launches": r["launches"] * args.steps,
         "clocks": r["clocks"],
         "roofline": r["roofline"],
         "kernels": r["kernels"],
+        "device_time": _device_time(r, args.steps),
         "e2e": {"value": round(world * psteps / e2e_t, 1) if t_e2e is not None else None, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": ("evc_set_values(V" if W.kind == "stencil" else "evc_set_values(CSR values")
@@ -575,10 +609,11 @@ def run_serving(args):
     Ns = [32, 40, 48, 64, 80, 96, 112, 128]
     h = 0.3
     ctxs, vmin = [], []
+    pk = {"identity": evc.EVC_PREC_IDENTITY, "jacobi": evc.EVC_PREC_JACOBI}[args.serving_precond]
     for N in Ns:
         V = inputs.gaussian_wells(N, h, nwells=32, seed=1)
         c = evc.Context.stencil(N, h, 2, V, precision=evc.EVC_MIXED)
-        c.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        c.set_precond(pk, 1e-3)
         # no tolerance stop before step 10: the first Ritz values have not yet
         # reached the low end of the spectrum, where L stagnates near zero
         evc.evc_set_option(c.h, evc.EVC_OPT_MIN_STEPS, 10)
@@ -588,73 +623,78 @@ def run_serving(args):
     budget = int(0.85 * free)
     srv = evc.evc_server_create(budget, slots=args.slots, max_batch=16)
     mids = [evc.evc_server_add_matrix(srv, c.h) for c in ctxs]
-    rng = np.random.default_rng(3 + rank)
-    nreq, rate = args.requests, args.rate
-    gaps = rng.exponential(1.0 / rate, size=nreq)
-    arrive = np.cumsum(gaps)
-    reqs = []
-    for q in range(nreq):
-        mi = int(rng.integers(0, len(Ns)))
-        a, b = np.sort(rng.uniform(0.0, 4.0, size=2))
-        if b - a < 0.05:
-            b = a + 0.05
-        reqs.append(dict(matrix_id=mids[mi], xi=vmin[mi] + float(a), eta=vmin[mi] + float(b),
-                         nprobe=int(rng.choice([32, 64, 128])), maxsteps=30,
-                         tol=float(rng.choice([0.25, 0.5])), seed=3))
     # warm-up: one request per matrix size, not timed
     for mi in mids:
         tk = evc.evc_server_submit(srv, mi, vmin[mi], vmin[mi] + 1.0, 32, 5, 0.0, 3)
         evc.evc_server_wait(srv, tk)
+
+    def phase(nreq, rate, seed):
+        """nreq Poisson arrivals at `rate` per second; returns the results."""
+        rng = np.random.default_rng(seed)
+        arrive = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+        reqs = []
+        for q in range(nreq):
+            mi = int(rng.integers(0, len(Ns)))
+            a, b = np.sort(rng.uniform(0.0, 4.0, size=2))
+            if b - a < 0.05:
+                b = a + 0.05
+            reqs.append(dict(matrix_id=mids[mi], xi=vmin[mi] + float(a), eta=vmin[mi] + float(b),
+                             nprobe=int(rng.choice([32, 64, 128])), maxsteps=30,
+                             tol=float(rng.choice([0.25, 0.5])), seed=3))
+        st0 = evc.evc_server_stats(srv)
+        tickets = [None] * nreq
+        t0 = time.perf_counter()
+
+        def submitter():
+            for q in range(nreq):
+                dt = arrive[q] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[q] = evc.evc_server_submit(srv, **reqs[q])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        results = [evc.evc_server_wait(srv, tickets[q]) for q in range(nreq)]
+        wall = time.perf_counter() - t0
+        st = evc.evc_server_stats(srv)
+        ok = [(q, r) for q, (rc, r) in zip(reqs, results) if rc == evc.EVC_OK]
+        lat = np.array([r["t_done"] - r["t_submit"] for _, r in ok])
+        span = max(r["t_done"] for _, r in ok) - min(r["t_submit"] for _, r in ok)
+        psteps = sum(q["nprobe"] * sum(r["steps"]) for q, r in ok)
+        return {"offered_rps": rate, "requests": nreq, "completed": len(ok),
+                "failed": nreq - len(ok), "throughput_rps": round(len(ok) / span, 2),
+                "p50_ms": round(1000 * float(np.percentile(lat, 50)), 2),
+                "p99_ms": round(1000 * float(np.percentile(lat, 99)), 2),
+                "mean_batch": round(float(np.mean([r["batch_size"] for _, r in ok])), 2),
+                "merged": st["merged"] - st0["merged"], "batches": st["batches"] - st0["batches"],
+                "wall_s": round(wall, 2), "span_s": round(span, 3),
+                "mean_steps": round(float(np.mean([np.mean(r["steps"]) for _, r in ok])), 2),
+                "probe_steps": psteps}
+
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    tickets = [None] * nreq
-    t0 = time.perf_counter()
-
-    def submitter():
-        for q in range(nreq):
-            dt = arrive[q] - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            tickets[q] = evc.evc_server_submit(srv, **reqs[q])
-
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    results = []
-    for q in range(nreq):
-        rc, r = evc.evc_server_wait(srv, tickets[q])
-        results.append((rc, r))
-    wall = time.perf_counter() - t0
+    main = phase(args.requests, args.rate, 3 + rank)
     clk = clocks.stop()
+    low = phase(args.low_requests, args.low_rate, 103 + rank) if args.low_rate > 0 else None
     st = evc.evc_server_stats(srv)
     evc.evc_server_destroy(srv)
     for c in ctxs:
         c.close()
-    ok = [r for rc, r in results if rc == evc.EVC_OK]
-    lat = np.array([r["t_done"] - r["t_submit"] for r in ok])
-    first = min(r["t_submit"] for r in ok)
-    last = max(r["t_done"] for r in ok)
-    span = last - first
-    psteps = sum(q["nprobe"] * sum(r["steps"]) for q, (rc, r) in zip(reqs, results) if rc == 0)
-    value = psteps / span
+    value = main["probe_steps"] / main["span_s"]
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-            "steps": nreq, "warmup": len(mids), "ms_per_step": round(1000 * span / max(1, len(ok)), 3),
+            "steps": args.requests, "warmup": len(mids),
+            "ms_per_step": round(1000 * main["span_s"] / max(1, main["completed"]), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "serving_8x_fd_7pt_32^3-128^3_jacobi", "requests": nreq,
-                       "offered_rps": rate, "slots": args.slots, "max_batch": 16,
-                       "hbm_budget_GB": round(budget / 1e9, 1),
+            "config": {"workload": f"serving_8x_fd_7pt_32^3-128^3_{args.serving_precond}",
+                       "requests": args.requests, "offered_rps": args.rate, "slots": args.slots,
+                       "max_batch": 16, "hbm_budget_GB": round(budget / 1e9, 1),
                        "probes": [32, 64, 128], "tol": [0.25, 0.5], "maxsteps": 30,
-                       "min_steps": 10,
+                       "min_steps": 10, "precond": args.serving_precond,
                        "step": "one request (2 shifts x m probes, early stop)"},
-            "serving": {"completed": len(ok), "failed": nreq - len(ok),
-                        "throughput_rps": round(len(ok) / span, 2),
-                        "p50_ms": round(1000 * float(np.percentile(lat, 50)), 2),
-                        "p99_ms": round(1000 * float(np.percentile(lat, 99)), 2),
-                        "mean_batch": round(float(np.mean([r["batch_size"] for r in ok])), 2),
-                        "merged": st["merged"], "batches": st["batches"],
-                        "peak_hbm_GB": round(st["peak_bytes"] / 1e9, 2), "wall_s": round(wall, 2),
-                        "mean_steps": round(float(np.mean([np.mean(r["steps"]) for r in ok])), 2)},
+            "serving": dict(main, peak_hbm_GB=round(st["peak_bytes"] / 1e9, 2)),
+            "serving_low_rate": low,
             "clocks": clk,
             "e2e": {"value": round(value, 1), "unit": UNIT,
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * 3,
@@ -781,15 +821,25 @@ def main():
                     help="concurrent chunk groups of the stencil passes (with --no-autotune)")
     ap.add_argument("--csr-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="threads per block of the CSR pass (with --no-autotune)")
+    ap.add_argument("--maxsteps", type=int, default=0,
+                    help="profiling aid: run the workload with this many Lanczos steps instead "
+                         "of its own (a smaller device footprint for ncu captures)")
     ap.add_argument("--method", default="lanczos", choices=["lanczos", "arnoldi"],
                     help="estimator: preconditioned Lanczos (default) or the Arnoldi-type variant")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per s")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: server slots")
+    ap.add_argument("--serving-precond", default="identity", choices=["identity", "jacobi"],
+                    help="serving workload: preconditioner of the resident Hamiltonians")
+    ap.add_argument("--low-rate", type=float, default=50.0,
+                    help="serving workload: a second, lighter phase at this rate (0: none)")
+    ap.add_argument("--low-requests", type=int, default=500,
+                    help="serving workload: requests of the lighter phase")
     ap.add_argument("--cheb-form", default="factored", choices=["factored", "clenshaw"],
                     help="how the Chebyshev preconditioner polynomial is applied")
     args = ap.parse_args()
     _CHEB_FORM[0] = 0 if args.cheb_form == "factored" else 1
+    _MAXSTEPS[0] = args.maxsteps
     _METHOD[0] = 0 if args.method == "lanczos" else 1
     _SHAPES["patch"], _SHAPES["zb"] = args.stencil_patch, args.stencil_zb
     _SHAPES["groups"] = args.stencil_groups

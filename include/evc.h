@@ -184,8 +184,10 @@ int evc_sync(evc_ctx* ctx);
 /* The tridiagonal matrices of the last call (Sec. 3, Eq. Tk), for
  * diagnostics: alpha[c*maxsteps + i] = alpha_{i+1}, beta[c*(maxsteps+1) + i]
  * = beta_{i+1} (beta_1 = 0) of column c = s*nprobe + j; kdone[c] = steps the
- * column completed (< maxsteps after a Lanczos breakdown).  Host arrays of
- * the sizes implied by the last call's nshift, nprobe and maxsteps.          */
+ * column completed (< maxsteps after a Lanczos breakdown or its shift's stop).
+ * After a shared-Krylov call (EVC_OPT_SHARED_KRYLOV) the tridiagonal of
+ * column s*nprobe + j is probe j's J_k(A) - shifts[s] I.  Host arrays of the
+ * sizes implied by the last call's nshift, nprobe and maxsteps.              */
 int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
 
 /* Options.
@@ -247,6 +249,19 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       idle.  At most one group per chunk.  Results are
  *                       bitwise unchanged.  With profiling on, each segment is
  *                       timed as one span record (see evc_prof_rec).
+ *   EVC_OPT_SHARED_KRYLOV: 1 (default): a call with several shifts under the
+ *                       identity preconditioner (Lanczos) runs one Lanczos
+ *                       process per probe, on A itself, and reads every shift's
+ *                       quadrature from its J_k: the Krylov space of A - tau I
+ *                       does not depend on tau and J_k(A - tau I) = J_k(A) -
+ *                       tau I, so shift tau sums the Gauss weights of the Ritz
+ *                       values below tau (Sec. 3, Eq. gauss_quad).  The m probe
+ *                       columns run while any shift runs; a shift's stop rule
+ *                       and results are its own.  Results equal per-shift runs
+ *                       up to rounding.  0: one run per shift.  Other
+ *                       preconditioners depend on the shift (Jacobi) or make the
+ *                       operator M A M - tau M^2 (Chebyshev), whose Krylov space
+ *                       moves with tau: they always run per shift.
  *   EVC_OPT_CSR_THREADS: CSR contexts: threads per block of the CSR pass, 128,
  *                       256 (default) or 512.  Results are unchanged.
  *   EVC_OPT_METHOD    : EVC_METHOD_LANCZOS (default): Algorithms 1-2 on
@@ -273,7 +288,8 @@ enum {
     EVC_OPT_CSR_THREADS = 10,
     EVC_OPT_METHOD = 11,
     EVC_OPT_STENCIL_PATCH = 12,
-    EVC_OPT_STENCIL_GROUPS = 13
+    EVC_OPT_STENCIL_GROUPS = 13,
+    EVC_OPT_SHARED_KRYLOV = 14
 };
 enum { EVC_METHOD_LANCZOS = 0, EVC_METHOD_ARNOLDI = 1 };
 enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };
@@ -351,12 +367,15 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
  *
  * A scheduler thread keeps the waiting requests in arrival order.  Whenever
  * one of `slots` execution slots is idle it forms a batch: the oldest waiting
- * request plus later requests that can share its launch (same matrix,
- * nprobe, maxsteps, tol and seed), at most max_batch of them and only as many
- * as fit the HBM budget (the batch's workspace, evc_workspace_bytes of
- * 2 shifts per request).  A batch is one evc_count_slices on the slot's own
- * stream, so batches on different slots overlap on the device; memory and
- * slots return when a batch ends and waiting requests are admitted then.
+ * request plus later requests that can share its launch (same matrix, nprobe
+ * and seed; tol and maxsteps may differ), at most max_batch of them and only
+ * as many as fit the HBM budget (the batch's workspace, evc_workspace_bytes
+ * of 2 shifts per request at the batch's largest maxsteps).  A batch is one
+ * batched count on the slot's own stream in which every shift keeps its own
+ * request's tol and maxsteps, so batches on different slots overlap on the
+ * device; under the identity preconditioner the batch's shifts share one
+ * Lanczos run per probe (EVC_OPT_SHARED_KRYLOV).  Memory and slots return
+ * when a batch ends and waiting requests are admitted then.
  * The oldest request is never overtaken; one that cannot fit even with
  * nothing running fails with EVC_ENOMEM.  Each request's result equals the
  * result of the same request run alone (columns are independent and every

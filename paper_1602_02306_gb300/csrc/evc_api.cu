@@ -30,14 +30,14 @@ namespace {
 enum { OP_CSR = 0, OP_STENCIL = 1 };
 
 struct GraphKey {
-    int S = -1, m = -1, kmax = -1, adaptive = -1, prec_version = -1, profile = -1;
+    int S = -1, m = -1, kmax = -1, adaptive = -1, prec_version = -1, profile = -1, shared = -1;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool operator==(const GraphKey& o) const
     {
         return S == o.S && m == o.m && kmax == o.kmax && adaptive == o.adaptive &&
                prec_version == o.prec_version && profile == o.profile && ws == o.ws &&
-               ws_bytes == o.ws_bytes;
+               ws_bytes == o.ws_bytes && shared == o.shared;
     }
 };
 
@@ -82,6 +82,7 @@ struct evc_ctx {
     int sten_groups = 1;
     cudaStream_t aux[kMaxStencilGroups - 1] = {};
     int method = EVC_METHOD_LANCZOS;
+    int shared_krylov = 1;        // identity preconditioner: shifts share one run
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
     int min_steps = 3;
@@ -169,13 +170,22 @@ struct Layout {
 
 bool uses_work(const evc_ctx* c) { return c->op == OP_STENCIL && c->prec == EVC_PREC_CHEB_KINETIC; }
 bool uses_jac(const evc_ctx* c) { return c->prec == EVC_PREC_JACOBI; }
+// Shared mode (see Run): without a preconditioner the Lanczos process on
+// A - tau I is the one on A shifted by tau, so several shifts read one run.
+bool use_shared(const evc_ctx* c, int S)
+{
+    return S > 1 && c->shared_krylov && c->prec == EVC_PREC_IDENTITY &&
+           c->method == EVC_METHOD_LANCZOS;
+}
 
 // Carve the workspace into the run's arrays with one cursor, so the size
 // query (base = 0) and the real carving can never disagree.  Every array
 // starts on a 256-byte boundary.
 size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void** work)
 {
-    const int ncol_real = S * m;
+    const bool shared = use_shared(c, S);
+    const int Sop = shared ? 1 : S;
+    const int ncol_real = shared ? m : S * m;
     const int nchunk = (ncol_real + CW - 1) / CW;
     const int ncol = nchunk * CW;
     const int nblk = choose_nblk(c->n, c->reorth_rows);
@@ -193,6 +203,9 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.kmax = kmax;
     r.ncol = ncol;
     r.ncol_real = ncol_real;
+    r.shared = shared ? 1 : 0;
+    r.nq = S * m;
+    r.Sop = Sop;
     r.nchunk = nchunk;
     r.nblk = nblk;
     r.slot_stride = c->n * CW;
@@ -200,8 +213,8 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.basis = take((size_t)nchunk * (kmax + 1) * vec);
     void* w = uses_work(c) ? take(3 * (size_t)nchunk * vec) : nullptr;
     if (work) *work = w;
-    r.jac = uses_jac(c) ? take((size_t)S * c->n * c->tsize) : nullptr;
-    r.dsh = c->op == OP_CSR ? take((size_t)S * c->n * c->tsize) : nullptr;
+    r.jac = uses_jac(c) ? take((size_t)Sop * c->n * c->tsize) : nullptr;
+    r.dsh = c->op == OP_CSR ? take((size_t)Sop * c->n * c->tsize) : nullptr;
     auto D = [&](size_t cnt) { return reinterpret_cast<double*>(take(cnt * 8)); };
     auto I = [&](size_t cnt) { return reinterpret_cast<int*>(take(cnt * 4)); };
     r.sigma = D(ncol);
@@ -211,8 +224,8 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.g = D((size_t)kmax * ncol);
     r.ppc = D(ncol);
     r.colscale = D(ncol);
-    r.quad = D(ncol);
-    r.quad_final = D(ncol);
+    r.quad = D((size_t)S * m);
+    r.quad_final = D((size_t)S * m);
     r.probe_id = reinterpret_cast<int64_t*>(take((size_t)ncol * 8));
     r.shift_of = I(ncol);
     r.kdone = I(ncol);
@@ -222,6 +235,9 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.Lfinal = D(S);
     r.steps = I(S);
     r.sdone = I(S);
+    r.stol = D(S);
+    r.skmax = I(S);
+    r.opshift = D(Sop);
     r.chunk_active = I(nchunk);
     r.cnt_upd = I(nchunk);
     r.nactive = I(kmax + 1);
@@ -232,7 +248,6 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     r.part_nrm = D((size_t)nchunk * nblk_max * CW);
     r.err = I(1);
     r.seed = reinterpret_cast<uint64_t*>(take(8));
-    r.tol = D(1);
     r.breakdown_rel = c->precision == EVC_FP64 ? 1e-12 : 1e-6;
     r.ga = c->quad_rule == EVC_QUAD_GA ? 1 : 0;
     r.min_steps = c->min_steps;
@@ -637,7 +652,7 @@ int stencil(evc_ctx* ctx, const Run& r, int step, const StencilPass& p, bool jac
     const double vchunk = (double)r.n * CW * sizeof(T);
     const double per = vchunk * (2 + (p.x ? 1 : 0) + (p.prev ? 1 : 0) + (p.pp ? 1 : 0));
     double fixed = p.useV ? (double)r.n * sizeof(T) : 0.0;
-    if (jac) fixed += (double)r.S * r.n * sizeof(T);
+    if (jac) fixed += (double)r.Sop * r.n * sizeof(T);
     return rec(ctx, EVC_K_STENCIL, step, fixed, per,
                [&] { return launch_stencil_pass<T>(ctx->sten, r, p, jac, ctx->stream); });
 }
@@ -807,7 +822,7 @@ int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
     int rc;
     if (ctx->op == OP_CSR) {
         const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
-                             (double)r.S * r.n * sizeof(T);
+                             (double)r.Sop * r.n * sizeof(T);
         const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk;
         rc = rec(ctx, EVC_K_CSR, i, fixed, per,
                  [&] { return launch_csr_pass<T>(ctx->csr, r, i, false, st); });
@@ -837,7 +852,7 @@ int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
         });
     }
     if (!rc && uses_jac(ctx))
-        rc = rec(ctx, EVC_K_JACOBI, i, (double)r.S * r.n * sizeof(T), 2.0 * vchunk,
+        rc = rec(ctx, EVC_K_JACOBI, i, (double)r.Sop * r.n * sizeof(T), 2.0 * vchunk,
                  [&] { return launch_row_scale<T>(r, wout, r.chunk_stride, st); });
     return rc;
 }
@@ -854,7 +869,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         // Jacobi scales and (CSR) the shifted operator's diagonal, per shift
         const double vdiag = ctx->op == OP_STENCIL ? ctx->sten.cd : 0.0;
         const double outs = (r.jac ? 1.0 : 0.0) + (r.dsh ? 1.0 : 0.0);
-        rc = rec(ctx, EVC_K_JACOBI, 0, outs * r.S * r.n * sizeof(T) + r.n * 8.0, 0.0, [&] {
+        rc = rec(ctx, EVC_K_JACOBI, 0, outs * r.Sop * r.n * sizeof(T) + r.n * 8.0, 0.0, [&] {
             return launch_jacobi_scales<T>(r, ctx->op == OP_CSR ? ctx->csr.diag : nullptr,
                                            ctx->op == OP_STENCIL ? ctx->sten.V : nullptr, vdiag,
                                            ctx->jac_eps, uses_jac(ctx) && !r.arnoldi, st);
@@ -874,7 +889,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             // the CSR structure and values once; per chunk, one gathered 32-column
             // x row per stored entry, the output and q_{i-1}
             const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
-                                 (uses_jac(ctx) ? 2.0 : 1.0) * r.S * r.n * sizeof(T);
+                                 (uses_jac(ctx) ? 2.0 : 1.0) * r.Sop * r.n * sizeof(T);
             const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk * (1 + (qprev ? 1 : 0));
             rc = rec(ctx, EVC_K_CSR, i, fixed, per,
                      [&] { return launch_csr_pass<T>(ctx->csr, r, i, uses_jac(ctx), st); });
@@ -932,7 +947,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         const bool last = (i == r.kmax);
         if (!rc && (adaptive || last))
             rc = rec(ctx, EVC_K_FINISH, i, colb * (2.0 * i + 2), 0.0,
-                     [&] { return launch_finish(r, i, last, st); });
+                     [&] { return launch_finish(r, i, st); });
         if (!rc && adaptive)
             rc = rec(ctx, EVC_K_FINISH, i, colb, 0.0, [&] { return launch_active(r, i, st); });
     }
@@ -961,14 +976,16 @@ void drop_graph(evc_ctx* ctx)
 }
 
 // Validate, size the workspace, upload the per-call parameters and enqueue
-// (or replay) the run.  Results stay on the device.
+// (or replay) the run.  Results stay on the device.  tols / ksteps (either may
+// be null: tol / maxsteps for every shift) give each shift its own stop
+// tolerance and step limit.
 int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, double tol,
-              uint64_t seed)
+              uint64_t seed, const double* tols = nullptr, const int* ksteps = nullptr)
 {
     if (!ctx) return EVC_EINVAL;
     if (!shifts || S < 1) return fail(ctx, EVC_EINVAL, "need at least one shift");
     if (m < 1) return fail(ctx, EVC_EINVAL, "nprobe must be >= 1 (got %d)", m);
-    if (maxsteps < 1 || maxsteps > EVC_MAX_STEPS)
+    if (!ksteps && (maxsteps < 1 || maxsteps > EVC_MAX_STEPS))
         return fail(ctx, EVC_EINVAL, "maxsteps must be in [1, %d] (got %d)", EVC_MAX_STEPS, maxsteps);
     if ((int64_t)S * m > (int64_t)1 << 26) return fail(ctx, EVC_EINVAL, "too many columns");
     if ((uint64_t)m + CW > ((uint64_t)1 << 32)) return fail(ctx, EVC_EINVAL, "nprobe too large");
@@ -977,7 +994,15 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
     for (int s = 0; s < S; ++s)
         if (!std::isfinite(shifts[s])) return fail(ctx, EVC_EINVAL, "shift %d is not finite", s);
     if (!std::isfinite(tol)) return fail(ctx, EVC_EINVAL, "tol is not finite");
-    const int kmax = (int)std::min<int64_t>(maxsteps, ctx->n);
+    int kreq = ksteps ? 0 : maxsteps;
+    for (int s = 0; ksteps && s < S; ++s) {
+        if (ksteps[s] < 1 || ksteps[s] > EVC_MAX_STEPS)
+            return fail(ctx, EVC_EINVAL, "maxsteps of shift %d must be in [1, %d]", s, EVC_MAX_STEPS);
+        kreq = std::max(kreq, ksteps[s]);
+    }
+    for (int s = 0; tols && s < S; ++s)
+        if (!std::isfinite(tols[s])) return fail(ctx, EVC_EINVAL, "tol of shift %d is not finite", s);
+    const int kmax = (int)std::min<int64_t>(kreq, ctx->n);
     if (ctx->method == EVC_METHOD_ARNOLDI) {
         if (kmax > kArnoldiMaxSteps)
             return fail(ctx, EVC_EINVAL, "the Arnoldi method runs at most %d steps (got %d)",
@@ -1007,8 +1032,9 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
     void* work = nullptr;
     carve(ctx, S, m, kmax, static_cast<char*>(ctx->ws), r, &work);
 
-    // per-call parameters: sigma / shift_of / probe_id per column, shifts, seed, tol
-    const size_t pbytes = (size_t)L.ncol * (8 + 8 + 4) + (size_t)S * 8 + 64;
+    // per-call parameters: sigma / shift_of / probe_id per column; shifts, stop
+    // tolerance and step limit per shift; operator shifts; seed
+    const size_t pbytes = (size_t)L.ncol * (8 + 8 + 4) + (size_t)S * (8 + 8 + 4 + 8) + 64;
     // the previous call's parameter copies must have left the staging buffer
     if (ctx->param_ev) CU(cudaEventSynchronize(ctx->param_ev));
     int rc = ensure_pinned(ctx, &ctx->pinned, &ctx->pinned_bytes, pbytes);
@@ -1018,29 +1044,40 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
     int64_t* hpid = reinterpret_cast<int64_t*>(h + (size_t)L.ncol * 8);
     int* hsh = reinterpret_cast<int*>(h + (size_t)L.ncol * 16);
     double* hshifts = reinterpret_cast<double*>(h + (size_t)L.ncol * 20);
-    uint64_t* hseed = reinterpret_cast<uint64_t*>(h + (size_t)L.ncol * 20 + (size_t)S * 8);
-    double* htol = reinterpret_cast<double*>(hseed + 1);
+    double* hstol = hshifts + S;
+    double* hops = hstol + S;
+    int* hsk = reinterpret_cast<int*>(hops + S);
+    uint64_t* hseed = reinterpret_cast<uint64_t*>(h + (((size_t)L.ncol * 20 + (size_t)S * 28 + 7) & ~(size_t)7));
+    const int ncr = r.ncol_real;     // Lanczos columns: S*m, or m in shared mode
     for (int c = 0; c < L.ncol; ++c) {
-        const bool real = c < S * m;
-        const int s = real ? c / m : S - 1;
+        const bool real = c < ncr;
+        // shared mode: every column runs on A itself (operator shift 0)
+        const int s = r.shared ? 0 : (real ? c / m : S - 1);
         hsh[c] = s;
-        hsig[c] = shifts[s];
+        hsig[c] = r.shared ? 0.0 : shifts[s];
         // probe ids probe_offset + j; padding columns run extra probes, ignored
-        hpid[c] = ctx->probe_offset + (real ? c % m : (int64_t)m + (c - S * m));
+        hpid[c] = ctx->probe_offset + (real ? c % m : (int64_t)m + (c - ncr));
     }
-    for (int s = 0; s < S; ++s) hshifts[s] = shifts[s];
+    bool adaptive = false;
+    for (int s = 0; s < S; ++s) {
+        hshifts[s] = shifts[s];
+        hstol[s] = tols ? tols[s] : tol;
+        hsk[s] = (int)std::min<int64_t>(ksteps ? ksteps[s] : maxsteps, ctx->n);
+        adaptive |= hstol[s] > 0.0 || hsk[s] < kmax;
+    }
+    for (int s = 0; s < r.Sop; ++s) hops[s] = r.shared ? 0.0 : shifts[s];
     *hseed = seed;
-    *htol = tol;
     CU(cudaMemcpyAsync(r.sigma, hsig, (size_t)L.ncol * 8, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(r.probe_id, hpid, (size_t)L.ncol * 8, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(r.shift_of, hsh, (size_t)L.ncol * 4, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(r.shifts, hshifts, (size_t)S * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.stol, hstol, (size_t)S * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.skmax, hsk, (size_t)S * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(r.opshift, hops, (size_t)r.Sop * 8, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(r.seed, hseed, 8, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(r.tol, htol, 8, cudaMemcpyHostToDevice, ctx->stream));
     if (!ctx->param_ev) CU(cudaEventCreateWithFlags(&ctx->param_ev, cudaEventDisableTiming));
     CU(cudaEventRecord(ctx->param_ev, ctx->stream));
 
-    const bool adaptive = tol > 0.0;
     auto enqueue = [&]() -> int {
         ctx->recs.clear();
         ctx->evnext = 0;
@@ -1057,6 +1094,7 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
         k.profile = ctx->profile;
         k.ws = ctx->ws;
         k.ws_bytes = ctx->ws_bytes;
+        k.shared = r.shared;
         if (!(ctx->gexec && k == ctx->gkey)) {
             drop_graph(ctx);
             cudaGraph_t g = nullptr;
@@ -1208,6 +1246,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->reorth_rows = src->reorth_rows;
     c->sten_groups = src->sten_groups;
     c->method = src->method;
+    c->shared_krylov = src->shared_krylov;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
     c->probe_offset = src->probe_offset;
@@ -1216,6 +1255,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
 }
 
 cudaStream_t evc::ctx_stream(const evc_ctx* c) { return c->stream; }
+int evc::shares_krylov(const evc_ctx* c, int nshift) { return use_shared(c, nshift) ? 1 : 0; }
 
 // ================================================================== C ABI
 
@@ -1458,7 +1498,7 @@ int evc_count_slices_async(evc_ctx* ctx, const double* shifts, int nshift, int n
     if (rc) return rc;
     const Run& r = ctx->run;
     if (d_quad)
-        CU(cudaMemcpyAsync(d_quad, r.quad_final, (size_t)r.ncol_real * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(d_quad, r.quad_final, (size_t)r.nq * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     if (d_n_below)
         CU(cudaMemcpyAsync(d_n_below, r.Lfinal, (size_t)r.S * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     if (d_steps)
@@ -1476,30 +1516,55 @@ int evc_sync(evc_ctx* ctx)
     return check_device_error(ctx);
 }
 
+}  // extern "C"
+
+namespace {
+// Copy the last run's results to the caller's host buffers (any may be null)
+// after checking the device's error flag.
+int fetch_results(evc_ctx* ctx, double* n_below, double* per_probe_quad, int* steps_used)
+{
+    int rc;
+    const Run& r = ctx->run;
+    const size_t need = (size_t)r.nq * 8 + (size_t)r.S * 12 + 64;
+    rc = ensure_pinned(ctx, &ctx->pinres, &ctx->pinres_bytes, need);
+    if (rc) return rc;
+    char* h = static_cast<char*>(ctx->pinres);
+    double* hq = reinterpret_cast<double*>(h);
+    double* hL = hq + r.nq;
+    int* hs = reinterpret_cast<int*>(hL + r.S);
+    CU(cudaMemcpyAsync(hq, r.quad_final, (size_t)r.nq * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hL, r.Lfinal, (size_t)r.S * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hs, r.steps, (size_t)r.S * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    rc = check_device_error(ctx);
+    if (rc) return rc;
+    if (per_probe_quad) memcpy(per_probe_quad, hq, (size_t)r.nq * 8);
+    if (n_below) memcpy(n_below, hL, (size_t)r.S * 8);
+    if (steps_used) memcpy(steps_used, hs, (size_t)r.S * 4);
+    return EVC_OK;
+}
+}  // namespace
+
+int evc::count_slices_each(evc_ctx* ctx, const double* shifts, int nshift, int nprobe,
+                           const int* maxsteps, const double* tol, uint64_t seed, double* n_below,
+                           double* per_probe_quad, int* steps_used)
+{
+    if (!maxsteps || !tol) return fail(ctx, EVC_EINVAL, "per-shift step limits and tolerances");
+    int rc = run_async(ctx, shifts, nshift, nprobe, 0, 0.0, seed, tol, maxsteps);
+    if (rc) return rc;
+    return fetch_results(ctx, n_below, per_probe_quad, steps_used);
+}
+
+extern "C" {
+
 int evc_count_slices(evc_ctx* ctx, const double* shifts, int nshift, int nprobe, int maxsteps,
                      double tol, uint64_t seed, double* n_below, double* per_probe_quad,
                      int* steps_used)
 {
     int rc = run_async(ctx, shifts, nshift, nprobe, maxsteps, tol, seed);
     if (rc) return rc;
-    const Run& r = ctx->run;
-    const size_t need = (size_t)r.ncol_real * 8 + (size_t)r.S * 12 + 64;
-    rc = ensure_pinned(ctx, &ctx->pinres, &ctx->pinres_bytes, need);
-    if (rc) return rc;
-    char* h = static_cast<char*>(ctx->pinres);
-    double* hq = reinterpret_cast<double*>(h);
-    double* hL = hq + r.ncol_real;
-    int* hs = reinterpret_cast<int*>(hL + r.S);
-    CU(cudaMemcpyAsync(hq, r.quad_final, (size_t)r.ncol_real * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(hL, r.Lfinal, (size_t)r.S * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(hs, r.steps, (size_t)r.S * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    rc = check_device_error(ctx);
-    if (rc) return rc;
-    if (per_probe_quad) memcpy(per_probe_quad, hq, (size_t)r.ncol_real * 8);
-    if (n_below) memcpy(n_below, hL, (size_t)r.S * 8);
-    if (steps_used) memcpy(steps_used, hs, (size_t)r.S * 4);
-    return EVC_OK;
+    return fetch_results(ctx, n_below, per_probe_quad, steps_used);
 }
+
 
 int evc_count(evc_ctx* ctx, double xi, double eta, int nprobe, int maxsteps, double tol,
               uint64_t seed, double* estimate, double* per_probe_quad, int* steps_used)
@@ -1521,21 +1586,27 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone)
     if (!ctx) return EVC_EINVAL;
     if (!ctx->have_run) return fail(ctx, EVC_EINVAL, "no previous run");
     const Run& r = ctx->run;
-    const int K = r.kmax, nc = r.ncol, ncr = r.ncol_real;
-    std::vector<double> a((size_t)K * nc), b((size_t)(K + 1) * nc);
-    std::vector<int> kd(nc);
+    const int K = r.kmax, nc = r.ncol;
+    std::vector<double> a((size_t)K * nc), b((size_t)(K + 1) * nc), sh(r.S);
+    std::vector<int> kd(nc), st(r.S);
     CU(cudaMemcpyAsync(a.data(), r.alpha, a.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(b.data(), r.beta, b.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(kd.data(), r.kdone, kd.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(sh.data(), r.shifts, sh.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(st.data(), r.steps, st.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    for (int c = 0; c < ncr; ++c) {
-        const int done = kd[c];
+    // output column c = s*m + j; in shared mode it is the run's column j, with
+    // J(A - tau_s I) = J(A) - tau_s I, up to the step the shift stopped at
+    for (int c = 0; c < r.nq; ++c) {
+        const int s = c / r.m, lc = r.shared ? c % r.m : c;
+        const int done = r.shared ? (kd[lc] ? std::min(kd[lc], st[s]) : st[s]) : kd[lc];
+        const double off = r.shared ? sh[s] : 0.0;
         if (kdone) kdone[c] = done;
         for (int i = 0; i < K; ++i) {
-            if (alpha) alpha[(size_t)c * K + i] = i < done ? a[(size_t)i * nc + c] : 0.0;
-            if (beta) beta[(size_t)c * (K + 1) + i] = i <= done ? b[(size_t)i * nc + c] : 0.0;
+            if (alpha) alpha[(size_t)c * K + i] = i < done ? a[(size_t)i * nc + lc] - off : 0.0;
+            if (beta) beta[(size_t)c * (K + 1) + i] = i <= done ? b[(size_t)i * nc + lc] : 0.0;
         }
-        if (beta) beta[(size_t)c * (K + 1) + K] = K <= done ? b[(size_t)K * nc + c] : 0.0;
+        if (beta) beta[(size_t)c * (K + 1) + K] = K <= done ? b[(size_t)K * nc + lc] : 0.0;
     }
     return EVC_OK;
 }
@@ -1607,6 +1678,13 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
         if (value < 1 || value > kMaxStencilGroups)
             return fail(ctx, EVC_EINVAL, "stencil chunk groups must be in [1, %d]", kMaxStencilGroups);
         ctx->sten_groups = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_SHARED_KRYLOV) {
+        if (value != 0 && value != 1) return fail(ctx, EVC_EINVAL, "shared Krylov option must be 0 or 1");
+        ctx->shared_krylov = (int)value;
         ++ctx->prec_version;
         drop_graph(ctx);
         return EVC_OK;

@@ -38,6 +38,16 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { typedef float4 type; };
 template <> struct Vec16<double> { typedef double2 type; };
 
+// Row sums are accumulated entry by entry, acc = fma(a_rj, x_j m_j, acc), with
+// the product and the fused multiply-add rounded explicitly, so that every
+// specialisation of the pass (uniform-shift chunks or not, any block size)
+// gives bitwise the same rows: a column's result must not depend on which
+// kernel its batch ran.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 __device__ __forceinline__ Pack<T> ldg16(const T* p)
 {
@@ -109,9 +119,12 @@ csr_pass_kernel(CArgs a)
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 T sa = xa.v[w], sb = xb.v[w];
-                if (JAC && UNI) { sa *= ma; sb *= mb; }
-                if (JAC && !UNI) { sa *= __ldg(jr[w] + ca); sb *= __ldg(jr[w] + cb); }
-                acc[w] += va * sa + vb * sb;
+                if (JAC && UNI) { sa = mul_rn(sa, ma); sb = mul_rn(sb, mb); }
+                if (JAC && !UNI) {
+                    sa = mul_rn(sa, __ldg(jr[w] + ca));
+                    sb = mul_rn(sb, __ldg(jr[w] + cb));
+                }
+                acc[w] = fma_rn(vb, sb, fma_rn(va, sa, acc[w]));
             }
         }
         if (t < cnt) {
@@ -122,9 +135,9 @@ csr_pass_kernel(CArgs a)
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 T sa = xa.v[w];
-                if (JAC && UNI) sa *= ma;
-                if (JAC && !UNI) sa *= __ldg(jr[w] + ca);
-                acc[w] += va * sa;
+                if (JAC && UNI) sa = mul_rn(sa, ma);
+                if (JAC && !UNI) sa = mul_rn(sa, __ldg(jr[w] + ca));
+                acc[w] = fma_rn(va, sa, acc[w]);
             }
         }
     }
@@ -139,10 +152,10 @@ csr_pass_kernel(CArgs a)
     for (int w = 0; w < W; ++w) {
         const int c = c0 + w;
         T r = acc[w];
-        if (JAC) r *= __ldg(jr[UNI ? 0 : w] + row);
-        r += __ldg(dsh + (int64_t)a.shift_of[c] * n + row) * cen.v[w];
-        r *= (T)a.insc[c];
-        if (pp) r -= (T)a.ppc[c] * prev.v[w];
+        if (JAC) r = mul_rn(r, __ldg(jr[UNI ? 0 : w] + row));
+        r = fma_rn(__ldg(dsh + (int64_t)a.shift_of[c] * n + row), cen.v[w], r);
+        r = mul_rn(r, (T)a.insc[c]);
+        if (pp) r = fma_rn(-(T)a.ppc[c], prev.v[w], r);
         res.v[w] = r;
     }
     typename Vec16<T>::type o;

@@ -55,10 +55,22 @@ constexpr int kThreads = 256;          // threads per block of the streaming ker
 enum { DERR_NONE = 0, DERR_NUMERIC = 4, DERR_TIMEOUT = 5, DERR_BOUNDS = 7 };
 
 // One run (a call of evc_count_slices) -- device pointers and sizes.
+//
+// Shared mode (identity preconditioner, Lanczos): the Krylov space of A - tau I
+// does not depend on tau, and Algorithm 1 on A - tau I gives J_k(A) - tau I.
+// So the run keeps m Lanczos columns on A itself (operator shift 0) and every
+// shift tau_s reads its quadrature from the same J_k: sum over Ritz values
+// theta < tau_s.  Per-column arrays (basis, alpha, beta, ...) then hold the m
+// probes; per-(shift, probe) arrays (quad, quad_final) hold S*m entries,
+// c = s*m + j, as in the normal mode.
 struct Run {
     int64_t n;
     int S, m, kmax;          // shifts, probes, steps (kmax already clamped)
-    int ncol, ncol_real;     // padded / real columns
+    int ncol, ncol_real;     // padded / real Lanczos columns (S*m, or m when shared)
+    int shared;              // 1: all shifts read one Krylov run (see above)
+    int nq;                  // (shift, probe) quadratures: S*m
+    int Sop;                 // operator shifts: S (normal) or 1 (shared: tau = 0)
+    double* opshift;         // [Sop] shift of the operator the columns run on
     int nchunk;
     int nblk;                // row blocks per chunk in the reorth kernels
     int64_t slot_stride;     // n*CW elements
@@ -75,8 +87,8 @@ struct Run {
     double* ppc;             // [ncol]
     double* colscale;        // [ncol]
     int* kdone;              // [ncol]
-    double* quad;            // [ncol]  latest quadrature
-    double* quad_final;      // [ncol]  quadrature at the shift's stop step
+    double* quad;            // [nq]  latest quadrature per (shift, probe)
+    double* quad_final;      // [nq]  quadrature at the shift's stop step
     // per shift
     double* shifts;          // [S]
     double* Lprev;           // [S]  L_s(i-1)
@@ -84,6 +96,8 @@ struct Run {
     double* Lfinal;          // [S]
     int* steps;              // [S]
     int* sdone;              // [S]
+    double* stol;            // [S]  stop tolerance per shift (<= 0: none)
+    int* skmax;              // [S]  last step per shift (<= kmax)
     int* chunk_active;       // [nchunk]
     int* cnt_upd;            // [nchunk]  blocks done, update kernel (last block forms beta)
     int* nactive;            // [kmax+1]  chunks active during step i+1 (profiling)
@@ -93,13 +107,12 @@ struct Run {
     double* hbuf;            // [kmax][ncol]  h_j = q_j . w of the current step
     double* gram;            // [kmax(kmax+1)/2][ncol]  G_ab = q_a . q_b, a >= b
     double* part_nrm;        // [nchunk][nblk][CW]
-    void* jac;               // T[S][n]  (Jacobi scales, when used)
-    void* dsh;               // T[S][n]  CSR contexts: the diagonal of the shifted operator,
+    void* jac;               // T[Sop][n]  (Jacobi scales, when used)
+    void* dsh;               // T[Sop][n]  CSR contexts: the diagonal of the shifted operator,
                              //   (a_rr - sigma) m_r^2 (Lanczos with Jacobi) or a_rr - sigma,
                              //   formed in FP64 from the FP64 diagonal, then rounded
     // device scalars, rewritten before each replay
     uint64_t* seed;          // [1]
-    double* tol;             // [1]
     double breakdown_rel;
     int ga;                  // 1: generalized averaged Gauss quadrature (Sec. 3.4)
     int min_steps;           // no tolerance stop before this step
@@ -187,7 +200,7 @@ template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_coef(const Run& r, int i, cudaStream_t st);
-cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st);
+cudaError_t launch_finish(const Run& r, int i, cudaStream_t st);
 cudaError_t launch_active(const Run& r, int i, cudaStream_t st);
 
 // Host-side helpers.
@@ -199,5 +212,12 @@ struct evc_ctx;
 namespace evc {
 evc_ctx* clone_context(const evc_ctx* src);
 cudaStream_t ctx_stream(const evc_ctx* c);
+// evc_count_slices with a stop tolerance and a step limit per shift (the
+// request server merges requests whose tolerances and limits differ).
+int count_slices_each(evc_ctx* ctx, const double* shifts, int nshift, int nprobe,
+                      const int* maxsteps, const double* tol, uint64_t seed, double* n_below,
+                      double* per_probe_quad, int* steps_used);
+// 1 when calls with nshift shifts run in shared mode (see Run).
+int shares_krylov(const evc_ctx* ctx, int nshift);
 
 }  // namespace evc

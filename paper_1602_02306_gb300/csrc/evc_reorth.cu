@@ -77,6 +77,8 @@ __global__ void init_state_kernel(Run r)
         r.ppc[t] = 0.0;
         r.colscale[t] = 0.0;
         r.kdone[t] = 0;
+    }
+    if (t < r.nq) {
         r.quad[t] = 0.0;
         r.quad_final[t] = 0.0;
     }
@@ -104,7 +106,7 @@ __global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, doubl
     // a_rr - tau.  Both from the FP64 diagonal, rounded once at the end: near
     // a_rr = tau, m_r^2 = 1/(|a_rr - tau| + eps) amplifies an error in a_rr
     // by up to 1/eps, so neither may be formed from rounded values.
-    const int64_t total = (int64_t)r.S * r.n;
+    const int64_t total = (int64_t)r.Sop * r.n;
     T* jac = static_cast<T*>(r.jac);
     T* dsh = static_cast<T*>(r.dsh);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -112,7 +114,7 @@ __global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, doubl
         const int s = (int)(e / r.n);
         const int64_t row = e % r.n;
         const double d = diag ? diag[row] : (double)V[row] + vdiag;
-        const double x = d - r.shifts[s];
+        const double x = d - r.opshift[s];
         const double m2 = 1.0 / (fabs(x) + eps);
         if (jac) jac[e] = (T)sqrt(m2);
         if (dsh) dsh[e] = (T)(jac_form ? x * m2 : x);
@@ -567,36 +569,51 @@ reorth_update_kernel(Run r, int i)
 
 // Quadrature of every running column's J_i (Sec. 3, Eq. gauss_quad), or of
 // the extended J~_{2i-1} of the generalized averaged rule (Sec. 3.4,
-// Eq. GA_Tk) when r.ga is set.  One thread per column; the eigensolver
-// scratch (3 x rule size per column) lives in shared memory.
+// Eq. GA_Tk) when r.ga is set.  One thread per Lanczos column; the
+// eigensolver scratch (3 x rule size per column) lives in shared memory.  In
+// shared mode one decomposition of the column's J_i serves every running
+// shift: the quadrature of shift s sums the weights of the Ritz values below
+// tau_s (J_i(A - tau I) = J_i(A) - tau I).
 __global__ void quad_kernel(Run r, int i)
 {
     extern __shared__ double qs[];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= r.ncol_real) return;
-    if (r.sdone[r.shift_of[c]]) return;
+    bool running;
+    if (r.shared) {
+        running = false;
+        for (int s = 0; s < r.S; ++s) running |= !r.sdone[s];
+    } else {
+        running = !r.sdone[r.shift_of[c]];
+    }
+    if (!running) return;
     const int k = r.kdone[c] ? min(r.kdone[c], i) : i;
     const int nb = blockDim.x;
     const int kk = r.ga ? 2 * r.kmax - 1 : r.kmax;
     double* d = qs + threadIdx.x;
     double* e = qs + (size_t)kk * nb + threadIdx.x;
     double* z = qs + (size_t)2 * kk * nb + threadIdx.x;
-    double q = r.ga ? tridiag_ga_quadrature(r.alpha + c, r.beta + c, r.ncol, k, (double)r.n, d, e, z, nb)
-                    : tridiag_gauss_quadrature(r.alpha + c, r.beta + c, r.ncol, k, (double)r.n, d, e,
-                                               z, nb);
-    if (q < 0.0) {
-        atomicExch(r.err, DERR_NUMERIC);
-        q = 0.0;
+    const int kr = tridiag_fill(r.alpha + c, r.beta + c, r.ncol, k, r.ga != 0, d, e, nb);
+    const bool ok = tridiag_eig_inplace(d, e, z, nb, kr);
+    if (!ok) atomicExch(r.err, DERR_NUMERIC);
+    if (r.shared) {
+        for (int s = 0; s < r.S; ++s)
+            if (!r.sdone[s])
+                r.quad[(int64_t)s * r.m + c] =
+                    ok && c < r.m ? quadrature_below(d, z, nb, kr, (double)r.n, r.shifts[s]) : 0.0;
+    } else {
+        r.quad[c] = ok ? quadrature_below(d, z, nb, kr, (double)r.n, 0.0) : 0.0;
     }
-    r.quad[c] = q;
 }
 
 // Per-shift mean L_s(i) = (1/m) sum_j quad_j in a fixed tree, and the stop
-// rule: a shift stops at the last step or, under a tolerance, at the first
-// i >= 2 with |L_s(i) - L_s(i-1)| <= tol.  A stopped shift's columns are
-// frozen (their later vectors become exact zeros).  One block per shift.
+// rule: a shift stops at its last step (skmax[s]) or, under its tolerance, at
+// the first step i >= max(3, min_steps) with |L_s(i) - L_s(i-1)| <= tol and
+// |L_s(i-1) - L_s(i-2)| <= tol.  In the normal mode a stopped shift's columns
+// are frozen (their later vectors become exact zeros); in shared mode the
+// Lanczos columns run on while any shift does.  One block per shift.
 __global__ void __launch_bounds__(kThreads)
-shift_kernel(Run r, int i, int last)
+shift_kernel(Run r, int i)
 {
     const int s = blockIdx.x;
     if (r.sdone[s]) return;
@@ -613,10 +630,8 @@ shift_kernel(Run r, int i, int last)
     }
     if (threadIdx.x == 0) {
         const double L = red[0] / r.m;
-        const double tol = *r.tol;
-        // stop rule: two consecutive changes of L_s within tol, not before
-        // step max(3, min_steps)
-        int st = last ? 1 : 0;
+        const double tol = r.stol[s];
+        int st = i >= r.skmax[s] ? 1 : 0;
         if (tol > 0.0 && i >= 3 && i >= r.min_steps && fabs(L - r.Lprev[s]) <= tol &&
             fabs(r.Lprev[s] - r.Lprev2[s]) <= tol)
             st = 1;
@@ -633,6 +648,7 @@ shift_kernel(Run r, int i, int last)
     if (stop)
         for (int c = cbeg + threadIdx.x; c < cend; c += blockDim.x) {
             r.quad_final[c] = r.quad[c];
+            if (r.shared) continue;
             r.ppc[c] = 0.0;
             for (int j = i; j <= r.kmax; ++j) r.scl[(int64_t)j * r.ncol + c] = 0.0;
             if (!r.kdone[c]) r.kdone[c] = i;
@@ -644,12 +660,23 @@ shift_kernel(Run r, int i, int last)
 __global__ void __launch_bounds__(kThreads) active_kernel(Run r, int i)
 {
     __shared__ int cnt[kThreads];
+    __shared__ int any_running;
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int s = 0; s < r.S; ++s) a |= !r.sdone[s];
+        any_running = a;
+    }
+    __syncthreads();
     int mine = 0;
     for (int ch = threadIdx.x; ch < r.nchunk; ch += blockDim.x) {
         int act = 0;
-        for (int l = 0; l < CW; ++l) {
-            const int c = ch * CW + l;
-            if (c < r.ncol_real && !r.sdone[r.shift_of[c]]) act = 1;
+        if (r.shared) {
+            act = any_running;
+        } else {
+            for (int l = 0; l < CW; ++l) {
+                const int c = ch * CW + l;
+                if (c < r.ncol_real && !r.sdone[r.shift_of[c]]) act = 1;
+            }
         }
         r.chunk_active[ch] = act;
         mine += act;
@@ -685,7 +712,7 @@ template <typename T>
 cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V, double vdiag,
                                  double eps, bool jac_form, cudaStream_t st)
 {
-    const int64_t total = (int64_t)r.S * r.n;
+    const int64_t total = (int64_t)r.Sop * r.n;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
     jacobi_scale_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(r, diag, static_cast<const T*>(V),
                                                              vdiag, eps, jac_form ? 1 : 0);
@@ -739,7 +766,7 @@ cudaError_t launch_update(const Run& r, int i, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st)
+cudaError_t launch_finish(const Run& r, int i, cudaStream_t st)
 {
     // The eigensolves are chains of dependent FP64 operations: spread the
     // columns over all 152 SMs (few threads per block) so each one has an
@@ -758,7 +785,7 @@ cudaError_t launch_finish(const Run& r, int i, bool last, cudaStream_t st)
     } else {
         quad_kernel<<<(r.ncol_real + qb - 1) / qb, qb, smem, st>>>(r, i);
     }
-    shift_kernel<<<r.S, kThreads, 0, st>>>(r, i, last ? 1 : 0);
+    shift_kernel<<<r.S, kThreads, 0, st>>>(r, i);
     return cudaGetLastError();
 }
 

@@ -4,10 +4,12 @@
 // Requests (matrix, xi, eta, probes, steps, tol, seed) arrive at any time.
 // A scheduler thread keeps them in arrival order and, whenever an execution
 // slot is idle, forms a batch: the oldest waiting request plus the later
-// ones that can share its launch (same matrix, probe count, step limit,
-// tolerance and seed), as many as the HBM budget and the batch limit allow.
-// The batch runs as one batched count (two shifts per request) on the
-// slot's own stream, so batches on different slots overlap on the device.
+// ones that can share its launch (same matrix, probe count and seed), as
+// many as the HBM budget and the batch limit allow.  The batch runs as one
+// batched count (two shifts per request, each with its request's tolerance
+// and step limit) on the slot's own stream, so batches on different slots
+// overlap on the device; under the identity preconditioner all shifts of the
+// batch read one Lanczos run per probe (shared Krylov mode).
 // A request that does not fit the remaining budget waits (first come, first
 // served: nothing overtakes it); memory and slots are returned as batches
 // finish, and waiting requests are admitted at once.  Every column of a
@@ -17,6 +19,7 @@
 #include "evc_internal.cuh"
 #include "../../include/evc.h"
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -77,10 +80,13 @@ struct evc_server {
 
 namespace {
 
+// Requests share a launch when they run the same probes on the same matrix;
+// each shift keeps its own stop tolerance and step limit, so tolerances and
+// limits may differ.  Under the identity preconditioner the merged shifts also
+// share the Lanczos columns themselves (shared Krylov mode).
 bool compatible(const Req* a, const Req* b)
 {
-    return a->matrix == b->matrix && a->nprobe == b->nprobe && a->maxsteps == b->maxsteps &&
-           a->tol == b->tol && a->seed == b->seed;
+    return a->matrix == b->matrix && a->nprobe == b->nprobe && a->seed == b->seed;
 }
 
 evc_ctx* clone_for(evc_server* s, Slot* sl, int matrix)
@@ -113,7 +119,9 @@ void schedule(evc_server* s)
         for (size_t idx = 0; idx < s->pending.size() && (int)take.size() < s->max_batch; ++idx) {
             Req* r = s->pending[idx];
             if (!compatible(head, r)) continue;
-            const size_t need = evc_workspace_bytes(c, 2 * ((int)take.size() + 1), r->nprobe, r->maxsteps);
+            int kmx = r->maxsteps;
+            for (size_t t : take) kmx = std::max(kmx, s->pending[t]->maxsteps);
+            const size_t need = evc_workspace_bytes(c, 2 * ((int)take.size() + 1), r->nprobe, kmx);
             if (need == 0 || s->used + need > s->budget) break;
             take.push_back(idx);
             bytes = need;
@@ -161,11 +169,13 @@ void run_batch(evc_server* s, Slot* sl, Batch* b)
     }
     const int R = (int)b->reqs.size();
     const int m = head->nprobe;
-    std::vector<double> shifts(2 * R), L(2 * R), quad((size_t)2 * R * m);
-    std::vector<int> steps(2 * R);
+    std::vector<double> shifts(2 * R), tols(2 * R), L(2 * R), quad((size_t)2 * R * m);
+    std::vector<int> steps(2 * R), kmax(2 * R);
     for (int q = 0; q < R; ++q) {
         shifts[2 * q] = b->reqs[q]->xi;
         shifts[2 * q + 1] = b->reqs[q]->eta;
+        tols[2 * q] = tols[2 * q + 1] = b->reqs[q]->tol;
+        kmax[2 * q] = kmax[2 * q + 1] = b->reqs[q]->maxsteps;
     }
     cudaSetDevice(s->device);
     int rc = EVC_OK;
@@ -179,17 +189,17 @@ void run_batch(evc_server* s, Slot* sl, Batch* b)
     }
     if (rc == EVC_OK) rc = evc_set_workspace(c, ws, b->bytes);
     if (rc == EVC_OK)
-        rc = evc_count_slices(c, shifts.data(), 2 * R, m, head->maxsteps, head->tol, head->seed,
-                              L.data(), quad.data(), steps.data());
+        rc = evc::count_slices_each(c, shifts.data(), 2 * R, m, kmax.data(), tols.data(),
+                                    head->seed, L.data(), quad.data(), steps.data());
     // A numeric failure is flagged once for the whole launch: run each request
     // of a merged batch alone (in the same workspace) so that only the request
     // whose own columns fail reports it, as it would have alone.
     std::vector<int> rcs(R, rc);
     if (rc == EVC_ENUMERIC && R > 1) {
         for (int q = 0; q < R; ++q)
-            rcs[q] = evc_count_slices(c, shifts.data() + 2 * q, 2, m, head->maxsteps, head->tol,
-                                      head->seed, L.data() + 2 * q, quad.data() + (size_t)2 * q * m,
-                                      steps.data() + 2 * q);
+            rcs[q] = evc::count_slices_each(c, shifts.data() + 2 * q, 2, m, kmax.data() + 2 * q,
+                                            tols.data() + 2 * q, head->seed, L.data() + 2 * q,
+                                            quad.data() + (size_t)2 * q * m, steps.data() + 2 * q);
     }
     evc_set_workspace(c, nullptr, 0);
     if (ws) {

@@ -14,15 +14,16 @@ struct Strided {
     __device__ double& operator[](int t) const { return p[(int64_t)t * s]; }
 };
 
-// Quadrature from a tridiagonal already in scratch: d[0..k) diagonal,
+// Eigen-decomposition of a tridiagonal already in scratch: d[0..k) diagonal,
 // e[0..k-1) off-diagonal (e[t] couples t and t+1), z scratch of k entries,
 // all with stride sstride.  Eigenvalues by the implicit symmetric QR
 // iteration with Wilkinson shifts on the unreduced trailing block; the first
 // components of the eigenvectors are carried along by applying every Givens
-// rotation to the vector e_1 (Golub & Welsch).  Returns
-// vnorm2 * sum_{theta<0} z(1)^2, or -1 if the iteration does not converge.
-__device__ inline double tridiag_quadrature_inplace(double* dp, double* ep, double* zp,
-                                                   int64_t sstride, int k, double vnorm2)
+// rotation to the vector e_1 (Golub & Welsch).  On return d holds the
+// eigenvalues theta_t and z their first components z_t(1); false if the
+// iteration did not converge.
+__device__ inline bool tridiag_eig_inplace(double* dp, double* ep, double* zp, int64_t sstride,
+                                           int k)
 {
     const Strided d{dp, sstride}, e{ep, sstride}, z{zp, sstride};
     for (int t = 0; t < k; ++t) z[t] = t == 0 ? 1.0 : 0.0;
@@ -37,7 +38,7 @@ __device__ inline double tridiag_quadrature_inplace(double* dp, double* ep, doub
             --hi;
             continue;
         }
-        if (++iter > max_iter) return -1.0;
+        if (++iter > max_iter) return false;
         int lo = hi - 1;
         while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
         // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
@@ -79,10 +80,54 @@ __device__ inline double tridiag_quadrature_inplace(double* dp, double* ep, doub
         e[hi - 1] = xv;
         z[hi] = zt;
     }
+    return true;
+}
+
+// Gauss quadrature of h(. - sigma) from a decomposed tridiagonal:
+// vnorm2 * sum_{theta_t < sigma} z_t(1)^2 (h(x) = 1 iff x < 0, Eq. h).
+__device__ inline double quadrature_below(const double* dp, const double* zp, int64_t sstride,
+                                          int k, double vnorm2, double sigma)
+{
     double s = 0.0;
-    for (int t = 0; t < k; ++t)
-        if (d[t] < 0.0) s += z[t] * z[t];                // h(theta) = 1 iff theta < 0
+    for (int t = 0; t < k; ++t) {
+        const double th = dp[(int64_t)t * sstride], z = zp[(int64_t)t * sstride];
+        if (th < sigma) s += z * z;
+    }
     return vnorm2 * s;
+}
+
+// Quadrature from a tridiagonal already in scratch (see tridiag_eig_inplace):
+// vnorm2 * sum_{theta<0} z(1)^2, or -1 if the iteration does not converge.
+__device__ inline double tridiag_quadrature_inplace(double* dp, double* ep, double* zp,
+                                                   int64_t sstride, int k, double vnorm2)
+{
+    if (!tridiag_eig_inplace(dp, ep, zp, sstride, k)) return -1.0;
+    return quadrature_below(dp, zp, sstride, k, vnorm2, 0.0);
+}
+
+// Fill scratch with J_k (Gauss) or the extended J~_{2k-1} (GA); returns the
+// order of the filled matrix.  Layouts as in the two quadratures below.
+__device__ inline int tridiag_fill(const double* alpha, const double* beta, int64_t astride, int k,
+                                   bool ga, double* dp, double* ep, int64_t sstride)
+{
+    if (!ga || k <= 1) {
+        for (int t = 0; t < k; ++t) {
+            dp[(int64_t)t * sstride] = alpha[(int64_t)t * astride];
+            ep[(int64_t)t * sstride] = t + 1 < k ? beta[(int64_t)(t + 1) * astride] : 0.0;
+        }
+        return k;
+    }
+    const int kk = 2 * k - 1;
+    for (int t = 0; t < kk; ++t) {
+        const int a = t < k ? t : 2 * k - 2 - t;
+        dp[(int64_t)t * sstride] = alpha[(int64_t)a * astride];
+        double off = 0.0;
+        if (t < k - 1) off = beta[(int64_t)(t + 1) * astride];
+        else if (t == k - 1) off = beta[(int64_t)k * astride];
+        else if (t < kk - 1) off = beta[(int64_t)(2 * k - 2 - t) * astride];
+        ep[(int64_t)t * sstride] = off;
+    }
+    return kk;
 }
 
 // Gauss quadrature of J_k (Sec. 3, Eq. gauss_quad): alpha[t*astride] =

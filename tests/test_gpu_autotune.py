@@ -49,6 +49,22 @@ def test_csr_threads_leave_results_unchanged():
             np.testing.assert_array_equal(ctx.count_slices([-0.5, 0.5], 33, 10)[1], ref)
 
 
+@pytest.mark.parametrize("prec", [evc.EVC_FP64, evc.EVC_MIXED])
+def test_csr_uniform_shift_chunks_match_mixed_chunks(prec):
+    # chunks whose 32 columns share a shift run a specialised CSR pass (one
+    # Jacobi scale per gathered entry); a column batched so that its chunk
+    # mixes shifts runs the general pass: the rows are bitwise the same
+    csr = I.powerlaw_symmetric(20011, cap=300, seed=2)
+    with evc.Context.csr(csr, precision=prec) as ctx:
+        ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+        alone = ctx.count_slices([0.5], 33, 10)[1]           # one shift: uniform chunks
+        mixed = ctx.count_slices([-0.5, 0.5], 33, 10)[1]     # 66 columns: chunk 1 mixes
+        np.testing.assert_array_equal(mixed[1], alone[0])
+        for nt in (128, 512):
+            ctx.set_option(evc.EVC_OPT_CSR_THREADS, nt)
+            np.testing.assert_array_equal(ctx.count_slices([-0.5, 0.5], 33, 10)[1], mixed)
+
+
 def test_reorth_rows_reorder_sums_only():
     shifts, m, k = [-2.5, 0.5], 36, 12
     V, ctx = _stencil_ctx(25)
