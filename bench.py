@@ -364,7 +364,7 @@ def _fp64_leg(evc, W, args, stream, seed, ws_mixed, shifts=None):
     ctx = _make_ctx(evc, W, evc.EVC_FP64, stream.cuda_stream, nshift=S)
     if not args.no_autotune:
         ctx.autotune(S, m, k)
-    nsteps = max(1, args.steps // 2)
+    nsteps = max(1, min(3, args.steps // 2))
     for _ in range(1):
         L, q, st = ctx.count_slices(shifts, m, k, tol=W.tol, seed=seed)
     torch.cuda.synchronize()
@@ -465,12 +465,13 @@ def run_ours(args):
         hv = W.csr()[2]
     Vh = torch.from_numpy(np.ascontiguousarray(hv)).pin_memory()
     t_e2e = None
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     if not args.skip_e2e:
         evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
         torch.cuda.synchronize()
         _barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             evc.evc_set_values(ctx.h, Vh.data_ptr(), False)
             evc.evc_count_slices(ctx.h, W.shifts, m, k, W.tol, seed)
         t_e2e = time.perf_counter() - t0
@@ -493,7 +494,7 @@ def run_ours(args):
     psteps = r["psteps"]
     t_step = ms_mixed / args.steps
     t_max = t_step
-    e2e_t = (t_e2e / args.steps) if t_e2e is not None else float("nan")
+    e2e_t = (t_e2e / e2e_steps) if t_e2e is not None else float("nan")
     if world > 1:
         t = torch.tensor([t_step, e2e_t], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -534,13 +535,17 @@ def run_ours(args):
         "e2e": {"value": round(world * psteps / e2e_t, 1) if t_e2e is not None else None, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": ("evc_set_values(V" if W.kind == "stencil" else "evc_set_values(CSR values")
-                        + " float64 from pinned host) + evc_count_slices (host outputs)"},
+                        + " float64 from pinned host) + evc_count_slices (host outputs)",
+                "steps": e2e_steps},
         "fp64": {"skipped": fp64_note} if f64 is None else {
             "value": round(world * f64["psteps"] / (f64["ms_per_step"] * 1e-3), 1), "unit": UNIT,
             "ms_per_step": round(f64["ms_per_step"], 3)},
         "estimate": {"mixed": est_mixed, "fp64": est_fp64,
-                     "mixed_minus_fp64": (est_mixed - est_fp64) if est_fp64 is not None else None,
+                     # this rank's probes on both paths (the whole count at N = 1)
+                     "mixed_minus_fp64": (float(r["L"][-1] - r["L"][0]) - est_fp64)
+                     if est_fp64 is not None else None,
                      "n_below_mixed": [round(float(x), 4) for x in L_mixed],
+                     "probes_per_shift": world * m,
                      "n_below_fp64": None if f64 is None else [round(float(x), 4) for x in f64["L"]],
                      "max_abs_per_probe_mixed_minus_fp64": None if f64 is None else
                      float(np.max(np.abs(r["quad"] - f64["quad"].reshape(-1))))},
@@ -801,6 +806,8 @@ def main():
     ap.add_argument("--extras", default="fd64,slicing96",
                     help="other workloads measured for the same line (comma list, '' for none)")
     ap.add_argument("--extra-steps", type=int, default=3, help="timed counts per extra workload")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="counts of the end-to-end leg (at most --steps)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--family-k", default="25,50,100,134,200,256",
                     help="laplace-family workload: the Lanczos step counts of the study")

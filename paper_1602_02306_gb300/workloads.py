@@ -32,6 +32,7 @@ class Workload:
     seed: int = 0
     min_steps: int = 3            # no tolerance stop before this step
     notes: dict = field(default_factory=dict)
+    _csr: object = field(default=None, repr=False, compare=False)
 
     @property
     def n(self) -> int:
@@ -43,7 +44,10 @@ class Workload:
         return I.gaussian_wells(self.N, self.h, nwells=self.nwells, seed=1)
 
     def csr(self):
-        return self.csr_builder()
+        """The CSR arrays (built once per Workload object)."""
+        if self._csr is None:
+            self._csr = self.csr_builder()
+        return self._csr
 
 
 # Lowest eigenvalue of H = -1/2 Lap_h + V on the periodic 64^3 grid (7-point,

@@ -89,22 +89,37 @@ def test_fd_hamiltonian_64_fullsize():
     assert abs((Lmx[-1] - Lmx[0]) - (L64[-1] - L64[0])) < MIXED_TOL
 
 
-def test_powerlaw_2m_fullsize():
-    # n = 2,000,000: per-probe quadratures near 8e5, far from converged at
-    # k = 50.  FP64 matches the oracle to 1e-12 relative.  The FP32 basis
-    # (backward error ~1e-7) moves unconverged Ritz values; the measured
-    # mixed error is ~3e-4 relative per probe, which is far above 0.5 in
-    # absolute terms here: the test records the bound that holds (1e-3).
+@pytest.fixture(scope="module")
+def powerlaw_2m_runs():
     W = workloads.powerlaw_2m()
     L64, q64, st64 = _gpu(W, evc.EVC_FP64)
     Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED)
+    return W, (L64, q64, st64), (Lmx, qmx, stmx)
+
+
+def test_powerlaw_2m_fullsize(powerlaw_2m_runs):
+    # n = 2,000,000: per-probe quadratures near 1e6, far from converged at
+    # k = 50.  FP64 matches the oracle per probe to 1e-12 relative.  The mixed
+    # path forms its Jacobi scales from the FP64 diagonal; its per-probe values
+    # stay within 1e-3 relative of the oracle and each n_below within 1e-5
+    # relative of FP64 (the bar the FP32 basis meets; see the next test).
+    W, (L64, q64, st64), (Lmx, qmx, stmx) = powerlaw_2m_runs
     P = _oracle_problem(W)
     ids = [0, 77, 127]
     ref = _sample_oracle(W, P, range(len(W.shifts)), ids, st64)
     for s in range(len(W.shifts)):
         np.testing.assert_allclose(q64[s, ids], ref[s], rtol=1e-12, atol=FP64_TOL)
         np.testing.assert_allclose(qmx[s, ids], ref[s], rtol=1e-3)
-    np.testing.assert_allclose(Lmx, L64, rtol=1e-3)
+    np.testing.assert_allclose(Lmx, L64, rtol=1e-5)
+
+
+@pytest.mark.xfail(strict=True, reason="FP32-mixed count on the 2M-row power-law workload is "
+                   "3.9 away from FP64 (measured -3.92 on an estimate of 77,414): FP32 storage "
+                   "of the Lanczos vectors leaves ~1e-5 relative per unconverged probe")
+def test_powerlaw_2m_mixed_estimate_within_half(powerlaw_2m_runs):
+    # the stated target: the FP32-mixed estimate within 0.5 of FP64's
+    W, (L64, _, _), (Lmx, _, _) = powerlaw_2m_runs
+    assert abs((Lmx[-1] - Lmx[0]) - (L64[-1] - L64[0])) < MIXED_TOL
 
 
 def test_slicing_96_fullsize():
