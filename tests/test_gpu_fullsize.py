@@ -134,6 +134,16 @@ def test_slicing_96_fullsize():
         assert np.max(np.abs(qmx[s, ids] - ref[s])) < MIXED_TOL
     # slice counts are differences of n_below; n_below is non-decreasing up to noise
     assert np.all(np.diff(Lmx) > -2.0)
+    # FP64 on three of the shifts (the FP64 basis of all 32 does not fit): each
+    # shift's columns and stop rule are independent of the others, so each is
+    # compared with the same shift of the mixed run
+    import dataclasses
+    Wf = dataclasses.replace(W, shifts=[W.shifts[s] for s in shifts])
+    Lf, qf, stf = _gpu(Wf, evc.EVC_FP64)
+    assert list(stf) == [int(stmx[s]) for s in shifts]
+    for j, s in enumerate(shifts):
+        assert abs(Lmx[s] - Lf[j]) < MIXED_TOL
+        np.testing.assert_allclose(qf[j, ids], ref[s], rtol=0, atol=FP64_TOL)
 
 
 def test_fd_hamiltonian_64_arnoldi_fullsize():
