@@ -89,6 +89,19 @@ def laplace32() -> Workload:
 FD96_LAMBDA_MIN = -2.767709970053203
 
 
+def slicing_96_profile() -> Workload:
+    """A smaller case of the 13-point passes for profiling: the 96^3
+    Hamiltonian of batched_slicing_96 with its first 2 shifts (4 chunks of
+    32 columns, each chunk vector 113 MB, still near L2's size), 4 steps --
+    about 3 GB on the device."""
+    W = batched_slicing_96()
+    W.name = "slicing_96^3_13pt_cheb8_S2_m64_k4"
+    W.shifts = W.shifts[:2]
+    W.maxsteps = 4
+    W.tol = 0.0
+    return W
+
+
 def batched_slicing_96() -> Workload:
     """Spectrum slicing of the 4th-order 13-point periodic 96^3 Hamiltonian
     (n = 884,736, h = 0.3, 32 wells): 32 shifts lambda_min + 8 s/32,
@@ -158,6 +171,7 @@ WORKLOADS = {
     "slicing96": batched_slicing_96,
     "powerlaw2m": powerlaw_2m,
     "powerlaw1m": powerlaw_1m_profile,
+    "slicing96x2": slicing_96_profile,
     "laplace2^-7": lambda: laplace_paper(7),
     "laplace2^-10": lambda: laplace_paper(10),
 }
