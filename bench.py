@@ -835,7 +835,7 @@ def main():
                     help="estimator: preconditioned Lanczos (default) or the Arnoldi-type variant")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per s")
-    ap.add_argument("--slots", type=int, default=4, help="serving workload: server slots")
+    ap.add_argument("--slots", type=int, default=2, help="serving workload: server slots")
     ap.add_argument("--serving-precond", default="identity", choices=["identity", "jacobi"],
                     help="serving workload: preconditioner of the resident Hamiltonians")
     ap.add_argument("--low-rate", type=float, default=50.0,

@@ -125,8 +125,9 @@ int evc_create_stencil(int N, double h, int order, const void* V, int V_is_fp32,
  * creation (val_is_fp32 / V_is_fp32).  Host (on_device = 0) or device
  * pointer; copied (converted to the context's type when it differs) into the
  * context's own device buffer on its stream; a CSR context re-forms its
- * float64 diagonal from the values as given.  EVC_EINVAL when the context
- * borrowed its values at creation.                                           */
+ * float64 diagonal from the values as given.  Host values of the other type
+ * pass through a device staging buffer the context keeps for later calls.
+ * EVC_EINVAL when the context borrowed its values at creation.               */
 int evc_set_values(evc_ctx* ctx, const void* values, int on_device);
 
 /* Choose the preconditioner (see the EVC_PREC_* list above).                */

@@ -62,6 +62,8 @@ struct evc_ctx {
     StencilOp sten{};
     void* own_V = nullptr;
     int val_fp32 = 0;             // type of the values given at creation (1: float32)
+    void* stage = nullptr;        // device staging of host values of the other type
+    size_t stage_bytes = 0;
     // preconditioner
     int prec = EVC_PREC_IDENTITY;
     double jac_eps = 1e-3;
@@ -292,6 +294,17 @@ __global__ void csr_diag_kernel(const int64_t* rp, const int32_t* col, const voi
     }
 }
 
+// Free the staging buffer of upload_values (after the stream has used it).
+int release_stage(evc_ctx* ctx)
+{
+    if (!ctx->stage) return EVC_OK;
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    return EVC_OK;
+}
+
 // Copy `count` matrix values (float32 when src_fp32, else float64; host or
 // device) into dst in the context's type.  With diag set (CSR contexts), also
 // form the FP64 diagonal from the values as given, before any rounding to the
@@ -316,11 +329,20 @@ int upload_values(evc_ctx* ctx, void* dst, const void* src, int64_t count, int s
         return form_diag(dst);
     }
     const void* dsrc = src;
-    void* tmp = nullptr;
     if (!on_device) {
-        CU(cudaMalloc(&tmp, count * ssz));
-        CU(cudaMemcpyAsync(tmp, src, count * ssz, cudaMemcpyHostToDevice, ctx->stream));
-        dsrc = tmp;
+        // host values of the other type pass through a device staging buffer
+        // the context keeps (grown on demand), so repeated updates allocate nothing
+        const size_t need = (size_t)count * ssz;
+        if (ctx->stage_bytes < need) {
+            CU(cudaStreamSynchronize(ctx->stream));
+            if (ctx->stage) cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+            CU(cudaMalloc(&ctx->stage, need));
+            ctx->stage_bytes = need;
+        }
+        CU(cudaMemcpyAsync(ctx->stage, src, need, cudaMemcpyHostToDevice, ctx->stream));
+        dsrc = ctx->stage;
     }
     int rc = form_diag(dsrc);
     if (rc) return rc;
@@ -332,10 +354,6 @@ int upload_values(evc_ctx* ctx, void* dst, const void* src, int64_t count, int s
         convert_kernel<double, float><<<blocks, 256, 0, ctx->stream>>>(
             static_cast<double*>(dst), static_cast<const float*>(dsrc), count);
     CU(cudaGetLastError());
-    if (tmp) {
-        CU(cudaStreamSynchronize(ctx->stream));
-        CU(cudaFree(tmp));
-    }
     return EVC_OK;
 }
 
@@ -1343,6 +1361,7 @@ int evc_create_csr(const evc_csr* A, int precision, void* stream, evc_ctx** out)
         rc = upload_values(ctx, ctx->own_val, A->val, nnz, A->val_is_fp32, A->on_device,
                            ctx->own_diag);
         if (rc) return cleanup(rc);
+        release_stage(ctx);   // kept only by evc_set_values, for repeated updates
         ctx->csr.val = ctx->own_val;
     }
     // visit order of the rows: by decreasing length, so the rows that share a
@@ -1409,6 +1428,7 @@ int evc_create_stencil(int N, double h, int order, const void* V, int V_is_fp32,
         }
         ctx->val_fp32 = V_is_fp32 ? 1 : 0;
         int rc = upload_values(ctx, ctx->own_V, V, ctx->n, V_is_fp32, on_device);
+        if (rc == EVC_OK) rc = release_stage(ctx);
         if (rc == EVC_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = EVC_ECUDA;
         if (rc) {
             evc_destroy(ctx);
@@ -1907,6 +1927,7 @@ void evc_destroy(evc_ctx* ctx)
     if (ctx->own_val) cudaFree(ctx->own_val);
     if (ctx->own_diag) cudaFree(ctx->own_diag);
     if (ctx->own_perm) cudaFree(ctx->own_perm);
+    if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->own_V) cudaFree(ctx->own_V);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->pinres) cudaFreeHost(ctx->pinres);
