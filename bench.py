@@ -326,10 +326,27 @@ def _measure(evc, W, args, stream, peak, peak_kind, steps, warmup, seed, tune=Tr
     psteps = float(m * int(np.sum(st)))
     return ctx, {"ms": ms, "L": L, "steps_used": st, "quad": q, "clocks": clk, "roofline": roof,
                  "kernels": per_kind, "launches": launches, "psteps": psteps, "ws": ws,
-                 "tuning": tuning, "kmax": k}
+                 "tuning": tuning, "kmax": k, "recs": recs}
 
 
 _WORLD = [1]
+
+
+def _early_stop_rates(evc, r):
+    """Rate of compulsory bytes of the streaming classes over the steps where
+    every shift runs against the steps after the first shift stopped: the
+    launches of later steps still cover the stopped chunks, whose blocks return
+    at once, so a drop in rate would be their cost."""
+    first = int(np.min(r["steps_used"]))
+    out = {"first_stop_step": first}
+    for kind, name in ((2, "stencil"), (4, "dots"), (6, "update")):
+        for label, sel in (("all_running", lambda st: st <= first),
+                           ("some_stopped", lambda st: st > first)):
+            rr = [x for x in r["recs"] if x[0] == kind and x[2] > 0 and sel(x[1])]
+            t = sum(x[2] for x in rr)
+            b = sum(x[3] for x in rr)
+            out[f"{name}_{label}_GBps"] = round(b / (t * 1e-3) / 1e9, 1) if t > 0 else None
+    return out
 
 
 def _device_time(r, steps):
@@ -400,6 +417,8 @@ def _extra(evc, name, args, stream, peak, peak_kind, seed):
            "roofline": r["roofline"], "kernels": r["kernels"], "clocks": r["clocks"],
            "tiles": r["tuning"], "gpu_launches_per_step": r["launches"],
            "device_time": _device_time(r, args.extra_steps)}
+    if W.tol > 0:
+        out["early_stop"] = _early_stop_rates(evc, r)
     if name == "slicing96" and not args.skip_fp64:
         # the FP64 basis of all 32 shifts does not fit beside anything; every
         # shift's columns (and its stop rule) are independent of the others, so

@@ -7,6 +7,7 @@ import json
 import os
 import shutil
 
+import numpy as np
 import pytest
 
 import bench
@@ -133,3 +134,18 @@ def test_clock_summary_flags_throttle_reasons(monkeypatch):
     assert out["reasons"] == ["hw_thermal_slowdown"] and out["samples"] == 1
     c2 = bench.ClockSampler(0)
     assert c2.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_early_stop_rates_split_at_the_first_stop():
+    # steps 1-2 with every shift running, step 3 after one stopped; the
+    # records carry the compulsory bytes of the chunks still active
+    recs = [(2, 1, 1.0, 5e9, 0), (2, 2, 1.0, 5e9, 0), (2, 3, 0.5, 2e9, 0),
+            (4, 1, 1.0, 6e9, 0), (4, 3, 1.0, 3e9, 0), (6, 2, -1.0, 1e9, 0)]
+    r = {"steps_used": np.array([2, 3]), "recs": recs}
+    out = bench._early_stop_rates(None, r)
+    assert out["first_stop_step"] == 2
+    assert out["stencil_all_running_GBps"] == pytest.approx(5000.0)
+    assert out["stencil_some_stopped_GBps"] == pytest.approx(4000.0)
+    assert out["dots_all_running_GBps"] == pytest.approx(6000.0)
+    assert out["dots_some_stopped_GBps"] == pytest.approx(3000.0)
+    assert out["update_all_running_GBps"] is None       # untimed record only

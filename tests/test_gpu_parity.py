@@ -132,6 +132,49 @@ def test_edge_sizes():
     assert np.max(np.abs(q - qr)) < FP64_TOL
 
 
+def test_one_by_one_and_two_by_two_matrices():
+    # n = 1: J_1 = [a - tau], so the count of one probe is 1 iff a < tau (the
+    # probe has ||v||^2 = 1); n = 2 with k clamped to 2 is exact (Proposition 1)
+    one = (np.array([0, 1]), np.array([0], dtype=np.int32), np.array([0.7]))
+    for prec in (evc.EVC_FP64, evc.EVC_MIXED):
+        L, q, st, _ = _gpu_csr(one, prec, evc.EVC_PREC_IDENTITY, 0, [0.5, 0.9], 3, 5)
+        np.testing.assert_array_equal(q, [[0.0] * 3, [1.0] * 3])
+        assert list(st) == [1, 1]
+    A = np.array([[1.0, 2.0], [2.0, -1.0]])            # eigenvalues +-sqrt(5)
+    csr = I.dense_to_csr(A)
+    P = O.Problem.csr_matrix(csr, O.PREC_NONE)
+    L, q, st, _ = _gpu_csr(csr, evc.EVC_FP64, evc.EVC_PREC_IDENTITY, 0, [-3.0, 0.0, 3.0], 4, 9)
+    qr, sr, Lr = O.count(P, [-3.0, 0.0, 3.0], 4, 9, seed=0)
+    assert np.max(np.abs(q - qr)) < FP64_TOL
+    # each probe's quadrature is exact: v^T h(A - tau I) v from the eigenvectors
+    w, U = np.linalg.eigh(A)
+    for s, tau in enumerate([-3.0, 0.0, 3.0]):
+        for j in range(4):
+            v = O.probe_vector(0, j, 2)
+            exact = float(np.sum((U[:, w < tau].T @ v) ** 2))
+            assert abs(q[s, j] - exact) < 1e-12
+
+
+def test_maximum_steps_both_rules():
+    # k = EVC_MAX_STEPS (256) on a random sparse indefinite n = 300 (no early
+    # breakdown): the Gauss rule on J_256 against the oracle; the averaged rule
+    # at k = 128 (a 255 x 255 extension; the oracle's cyclic Jacobi on the
+    # 511 x 511 extension of k = 256 takes about a minute per probe)
+    A = I.random_symmetric_dense(300, seed=17)
+    A[np.abs(A) < 1.0] = 0.0
+    A = 0.5 * (A + A.T) + np.diag(np.linspace(-2, 2, 300))
+    csr = I.dense_to_csr(A)
+    P = O.Problem.csr_matrix(csr, O.PREC_JACOBI)
+    for rule, k in ((evc.EVC_QUAD_GAUSS, evc.EVC_MAX_STEPS), (evc.EVC_QUAD_GA, 128)):
+        with evc.Context.csr(csr, precision=evc.EVC_FP64) as ctx:
+            ctx.set_precond(evc.EVC_PREC_JACOBI, 1e-3)
+            ctx.set_option(evc.EVC_OPT_QUADRATURE, rule)
+            L, q, st = ctx.count_slices([0.3], 3, k, seed=1)
+        qr, sr, Lr = O.count(P, [0.3], 3, k, seed=1, rule=rule)
+        assert list(st) == list(sr)
+        assert np.max(np.abs(q - qr)) < FP64_TOL
+
+
 # --------------------------------------------------------- CSR, mixed
 
 def test_csr_mixed_estimate_within_half():
