@@ -89,3 +89,23 @@ def test_shared_run_mixed_estimate():
     qr, sr, Lr = O.count(P, shifts, m, k, seed=0)
     assert abs((L[1] - L[0]) - (Lr[1] - Lr[0])) < 0.5
     assert np.max(np.abs(L - Lr)) < 0.5
+
+
+def test_shared_run_async_outputs():
+    # the asynchronous entry leaves every (shift, probe) quadrature on the
+    # device, as the synchronous one returns them
+    import torch
+    csr = _indefinite(200, seed=9)
+    shifts, m, k = [-0.7, 0.1, 0.9, 1.6], 40, 20
+    with evc.Context.csr(csr, precision=evc.EVC_MIXED) as ctx:
+        ctx.set_precond(evc.EVC_PREC_IDENTITY)
+        L, q, st = ctx.count_slices(shifts, m, k, tol=0.3, seed=2)
+        dq = torch.empty(len(shifts) * m, dtype=torch.float64, device="cuda")
+        dL = torch.empty(len(shifts), dtype=torch.float64, device="cuda")
+        ds = torch.empty(len(shifts), dtype=torch.int32, device="cuda")
+        evc.evc_count_slices_async(ctx.h, shifts, m, k, 0.3, 2, dL.data_ptr(), dq.data_ptr(),
+                                   ds.data_ptr())
+        evc.evc_sync(ctx.h)
+    np.testing.assert_array_equal(dq.cpu().numpy().reshape(len(shifts), m), q)
+    np.testing.assert_array_equal(dL.cpu().numpy(), L)
+    np.testing.assert_array_equal(ds.cpu().numpy(), st)
