@@ -275,7 +275,22 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       open left half-plane (Eq. arnoldi_quad), the same probes,
  *                       means and stop rule.  At most 90 steps; the Gauss rule
  *                       only; evc_get_tridiag does not apply.  Per-probe values
- *                       may be negative (the weights are complex).  */
+ *                       may be negative (the weights are complex).
+ *   EVC_OPT_TINV_LANCZOS: 0 (default): Algorithm 1 on C = M (A - tau I) M.
+ *                       1: the T^{-1}-inner-product Lanczos process of Sec. 4
+ *                       (Eq. lanT1), T (A - tau I) Y_k = Y_{k+1} J_{k+1,k} with
+ *                       Y^T T^{-1} Y = I, started from y_1 = M q_1, for the
+ *                       Jacobi preconditioner T = M^2 = diag(1/(|a_ii - tau| +
+ *                       eps)): the operator pass scales its output rows by T and
+ *                       not its gathered operands, and the reorthogonalisation's
+ *                       inner products and norms carry the weight T^{-1} =
+ *                       diag(|a_ii - tau| + eps).  Y_k = M Q_k, so J_k, the
+ *                       quadratures and the estimate equal Algorithm 1's up to
+ *                       rounding.  Identity preconditioner: the same process as
+ *                       Algorithm 1 (T = I).  The kinetic Chebyshev preconditioner
+ *                       and the Arnoldi method return EVC_EUNSUPPORTED at the
+ *                       count (the start z_1 = T^{-1} y_1 = M^{-1} q_1 would need
+ *                       a solve with p_d(K)).  */
 enum {
     EVC_OPT_GRAPH = 1,
     EVC_OPT_PROFILE = 2,
@@ -290,7 +305,8 @@ enum {
     EVC_OPT_METHOD = 11,
     EVC_OPT_STENCIL_PATCH = 12,
     EVC_OPT_STENCIL_GROUPS = 13,
-    EVC_OPT_SHARED_KRYLOV = 14
+    EVC_OPT_SHARED_KRYLOV = 14,
+    EVC_OPT_TINV_LANCZOS = 15
 };
 enum { EVC_METHOD_LANCZOS = 0, EVC_METHOD_ARNOLDI = 1 };
 enum { EVC_CHEB_FACTORED = 0, EVC_CHEB_CLENSHAW = 1 };

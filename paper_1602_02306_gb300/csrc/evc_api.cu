@@ -30,14 +30,15 @@ namespace {
 enum { OP_CSR = 0, OP_STENCIL = 1 };
 
 struct GraphKey {
-    int S = -1, m = -1, kmax = -1, adaptive = -1, prec_version = -1, profile = -1, shared = -1;
+    int S = -1, m = -1, kmax = -1, adaptive = -1, prec_version = -1, profile = -1, shared = -1,
+        tinv = -1;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool operator==(const GraphKey& o) const
     {
         return S == o.S && m == o.m && kmax == o.kmax && adaptive == o.adaptive &&
                prec_version == o.prec_version && profile == o.profile && ws == o.ws &&
-               ws_bytes == o.ws_bytes && shared == o.shared;
+               ws_bytes == o.ws_bytes && shared == o.shared && tinv == o.tinv;
     }
 };
 
@@ -85,6 +86,7 @@ struct evc_ctx {
     cudaStream_t aux[kMaxStencilGroups - 1] = {};
     int method = EVC_METHOD_LANCZOS;
     int shared_krylov = 1;        // identity preconditioner: shifts share one run
+    int tinv_lanczos = 0;         // Jacobi: the T^{-1}-inner-product process (Eq. lanT1)
     int prec_version = 0;
     int quad_rule = EVC_QUAD_GAUSS;
     int min_steps = 3;
@@ -172,6 +174,17 @@ struct Layout {
 
 bool uses_work(const evc_ctx* c) { return c->op == OP_STENCIL && c->prec == EVC_PREC_CHEB_KINETIC; }
 bool uses_jac(const evc_ctx* c) { return c->prec == EVC_PREC_JACOBI; }
+// T^{-1}-inner-product Lanczos (Eq. lanT1): with the Jacobi T = M^2 only; the
+// identity preconditioner makes it Algorithm 1 itself.
+bool uses_tinv(const evc_ctx* c)
+{
+    return c->tinv_lanczos && c->prec == EVC_PREC_JACOBI && c->method == EVC_METHOD_LANCZOS;
+}
+int pass_mode(const evc_ctx* c, const Run& r)
+{
+    if (!uses_jac(c)) return PM_NONE;
+    return r.tinv ? PM_TLEFT : PM_JACOBI;
+}
 // Shared mode (see Run): without a preconditioner the Lanczos process on
 // A - tau I is the one on A shifted by tau, so several shifts read one run.
 bool use_shared(const evc_ctx* c, int S)
@@ -217,6 +230,8 @@ size_t carve(const evc_ctx* c, int S, int m, int kmax, char* base, Run& r, void*
     if (work) *work = w;
     r.jac = uses_jac(c) ? take((size_t)Sop * c->n * c->tsize) : nullptr;
     r.dsh = c->op == OP_CSR ? take((size_t)Sop * c->n * c->tsize) : nullptr;
+    r.tinv = uses_tinv(c) ? 1 : 0;
+    r.tinvd = r.tinv ? take((size_t)Sop * c->n * c->tsize) : nullptr;
     auto D = [&](size_t cnt) { return reinterpret_cast<double*>(take(cnt * 8)); };
     auto I = [&](size_t cnt) { return reinterpret_cast<int*>(take(cnt * 4)); };
     r.sigma = D(ncol);
@@ -663,16 +678,16 @@ struct BTerm {
 };
 
 template <typename T>
-int stencil(evc_ctx* ctx, const Run& r, int step, const StencilPass& p, bool jac)
+int stencil(evc_ctx* ctx, const Run& r, int step, const StencilPass& p, int pmode)
 {
     // compulsory traffic: the stencil operand and every pointwise operand read
     // once, the output written once (per active chunk); V and Jacobi scales once
     const double vchunk = (double)r.n * CW * sizeof(T);
     const double per = vchunk * (2 + (p.x ? 1 : 0) + (p.prev ? 1 : 0) + (p.pp ? 1 : 0));
     double fixed = p.useV ? (double)r.n * sizeof(T) : 0.0;
-    if (jac) fixed += (double)r.Sop * r.n * sizeof(T);
+    if (pmode != PM_NONE) fixed += (double)r.Sop * r.n * sizeof(T);
     return rec(ctx, EVC_K_STENCIL, step, fixed, per,
-               [&] { return launch_stencil_pass<T>(ctx->sten, r, p, jac, ctx->stream); });
+               [&] { return launch_stencil_pass<T>(ctx->sten, r, p, pmode, ctx->stream); });
 }
 
 // y = p_d(K) x by Clenshaw's recurrence b_j = c_j x + 2 K~ b_{j+1} - b_{j+2},
@@ -715,7 +730,7 @@ int enqueue_cheb_factored(evc_ctx* ctx, const Run& r, int step, const void* x, i
             pa.k0 = g * (c - F.re);
             pa.out = Wa;
             pa.out_cs = wcs;
-            int rc = stencil<T>(ctx, r, step, pa, false);
+            int rc = stencil<T>(ctx, r, step, pa, PM_NONE);
             if (rc) return rc;
             p.in = Wa;
             p.in_cs = wcs;
@@ -741,7 +756,7 @@ int enqueue_cheb_factored(evc_ctx* ctx, const Run& r, int step, const void* x, i
             p.pp_cs = pp_cs;
             p.ppc = pp ? ppc : nullptr;
         }
-        int rc = stencil<T>(ctx, r, step, p, false);
+        int rc = stencil<T>(ctx, r, step, p, PM_NONE);
         if (rc) return rc;
         cur = dst;
         cur_cs = dst_cs;
@@ -811,7 +826,7 @@ int enqueue_cheb(evc_ctx* ctx, const Run& r, int step, const void* x, int64_t x_
         }
         p.out = dst;
         p.out_cs = dst_cs;
-        int rc = stencil<T>(ctx, r, step, p, false);
+        int rc = stencil<T>(ctx, r, step, p, PM_NONE);
         if (rc) return rc;
         if (final_) break;
         BTerm nb;
@@ -843,7 +858,7 @@ int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
                              (double)r.Sop * r.n * sizeof(T);
         const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk;
         rc = rec(ctx, EVC_K_CSR, i, fixed, per,
-                 [&] { return launch_csr_pass<T>(ctx->csr, r, i, false, st); });
+                 [&] { return launch_csr_pass<T>(ctx->csr, r, i, PM_NONE, st); });
     } else {
         StencilPass p{};
         p.in = qi;
@@ -855,7 +870,7 @@ int enqueue_arnoldi_operator(evc_ctx* ctx, const Run& r, int i, void* work)
         p.out = wout;
         p.out_cs = r.chunk_stride;
         rc = grouped(ctx, r, EVC_K_STENCIL, i, [&]() -> int {
-            int rc2 = stencil<T>(ctx, r, i, p, false);
+            int rc2 = stencil<T>(ctx, r, i, p, PM_NONE);
             if (!rc2 && ctx->prec == EVC_PREC_CHEB_KINETIC) {
                 T* W0 = static_cast<T*>(work);
                 T* W1 = W0 + (int64_t)r.nchunk * vstride;
@@ -882,17 +897,21 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
     const double vchunk = (double)r.n * CW * sizeof(T);
     const double colb = (double)r.ncol * 8;
     int rc = rec(ctx, EVC_K_INIT, 0, colb * 8, 0.0, [&] { return launch_init_state(r, st); });
-    if (!rc) rc = rec(ctx, EVC_K_INIT, 0, 0.0, vchunk, [&] { return launch_init_probe<T>(r, st); });
     if (!rc && (uses_jac(ctx) || ctx->op == OP_CSR)) {
         // Jacobi scales and (CSR) the shifted operator's diagonal, per shift
         const double vdiag = ctx->op == OP_STENCIL ? ctx->sten.cd : 0.0;
-        const double outs = (r.jac ? 1.0 : 0.0) + (r.dsh ? 1.0 : 0.0);
+        const double outs = (r.jac ? 1.0 : 0.0) + (r.dsh ? 1.0 : 0.0) + (r.tinvd ? 1.0 : 0.0);
         rc = rec(ctx, EVC_K_JACOBI, 0, outs * r.Sop * r.n * sizeof(T) + r.n * 8.0, 0.0, [&] {
             return launch_jacobi_scales<T>(r, ctx->op == OP_CSR ? ctx->csr.diag : nullptr,
                                            ctx->op == OP_STENCIL ? ctx->sten.V : nullptr, vdiag,
-                                           ctx->jac_eps, uses_jac(ctx) && !r.arnoldi, st);
+                                           ctx->jac_eps, r.arnoldi ? PM_NONE : pass_mode(ctx, r),
+                                           st);
         });
     }
+    // the probe (T^{-1} mode: y_1 = M q_1, after the scales)
+    if (!rc)
+        rc = rec(ctx, EVC_K_INIT, 0, r.tinv ? (double)r.Sop * r.n * sizeof(T) : 0.0, vchunk,
+                 [&] { return launch_init_probe<T>(r, st); });
     if (rc) return rc;
     T* basis = static_cast<T*>(r.basis);
     const int64_t vstride = r.n * CW;
@@ -906,11 +925,12 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
         } else if (ctx->op == OP_CSR) {
             // the CSR structure and values once; per chunk, one gathered 32-column
             // x row per stored entry, the output and q_{i-1}
+            const int pm = pass_mode(ctx, r);
             const double fixed = (double)ctx->nnz * (sizeof(T) + 4) + 8.0 * (r.n + 1) +
-                                 (uses_jac(ctx) ? 2.0 : 1.0) * r.Sop * r.n * sizeof(T);
+                                 (pm != PM_NONE ? 2.0 : 1.0) * r.Sop * r.n * sizeof(T);
             const double per = (double)ctx->nnz * CW * sizeof(T) + vchunk * (1 + (qprev ? 1 : 0));
             rc = rec(ctx, EVC_K_CSR, i, fixed, per,
-                     [&] { return launch_csr_pass<T>(ctx->csr, r, i, uses_jac(ctx), st); });
+                     [&] { return launch_csr_pass<T>(ctx->csr, r, i, pm, st); });
         } else if (ctx->prec == EVC_PREC_CHEB_KINETIC) {
             T* W0 = static_cast<T*>(work);
             T* W1 = W0 + (int64_t)r.nchunk * vstride;
@@ -929,7 +949,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
                 p.useSigma = 1;
                 p.out = W0;
                 p.out_cs = vstride;
-                rc2 = stencil<T>(ctx, r, i, p, false);
+                rc2 = stencil<T>(ctx, r, i, p, PM_NONE);
                 if (rc2) return rc2;
                 // w = M t - beta_i q_{i-1} into slot i
                 return enqueue_cheb<T>(ctx, r, i, W0, vstride, nullptr, W1, W2, wout,
@@ -949,10 +969,13 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             p.pp_cs = r.chunk_stride;
             p.ppc = qprev ? r.ppc : nullptr;
             rc = grouped(ctx, r, EVC_K_STENCIL, i,
-                         [&]() -> int { return stencil<T>(ctx, r, i, p, uses_jac(ctx)); });
+                         [&]() -> int { return stencil<T>(ctx, r, i, p, pass_mode(ctx, r)); });
         }
         if (rc) return rc;
-        rc = rec(ctx, EVC_K_DOTS, i, 0.0, vchunk * (i + 1), [&] { return launch_dots<T>(r, i, st); });
+        // T^{-1} mode: the weights T^{-1} once per chunk and kernel
+        const double tw = r.tinv ? vchunk / CW : 0.0;
+        rc = rec(ctx, EVC_K_DOTS, i, 0.0, vchunk * (i + 1) + tw,
+                 [&] { return launch_dots<T>(r, i, st); });
         if (!rc)
             rc = rec(ctx, EVC_K_REDUCE, i, colb * 3 * i, 2.0 * r.nblk * i * CW * 8,
                      [&] { return launch_reduce(r, i, st); });
@@ -960,7 +983,7 @@ int enqueue_all(evc_ctx* ctx, const Run& r, void* work, bool adaptive)
             rc = rec(ctx, EVC_K_REDUCE, i, colb * (2.0 * i + i * (i + 1) / 2), 0.0,
                      [&] { return launch_coef(r, i, st); });
         if (!rc)
-            rc = rec(ctx, EVC_K_UPDATE, i, 0.0, vchunk * (i + 2),
+            rc = rec(ctx, EVC_K_UPDATE, i, 0.0, vchunk * (i + 2) + tw,
                      [&] { return launch_update<T>(r, i, st); });
         const bool last = (i == r.kmax);
         if (!rc && (adaptive || last))
@@ -1027,7 +1050,14 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
                         kArnoldiMaxSteps, kmax);
         if (ctx->quad_rule != EVC_QUAD_GAUSS)
             return fail(ctx, EVC_EUNSUPPORTED, "the averaged Gauss rule is a Lanczos quadrature");
+        if (ctx->tinv_lanczos)
+            return fail(ctx, EVC_EUNSUPPORTED,
+                        "the T^-1-inner-product process is a Lanczos method (EVC_OPT_TINV_LANCZOS)");
     }
+    if (ctx->tinv_lanczos && ctx->prec == EVC_PREC_CHEB_KINETIC)
+        return fail(ctx, EVC_EUNSUPPORTED,
+                    "the T^-1-inner-product process needs a diagonal T (Jacobi): its start vector "
+                    "z_1 = M^-1 q_1 would need a solve with p_d(K)");
     Layout L = layout(ctx, S, m, kmax);
     if (L.total > ctx->ws_bytes) {
         if (!ctx->ws_owned && ctx->ws)
@@ -1113,6 +1143,7 @@ int run_async(evc_ctx* ctx, const double* shifts, int S, int m, int maxsteps, do
         k.ws = ctx->ws;
         k.ws_bytes = ctx->ws_bytes;
         k.shared = r.shared;
+        k.tinv = r.tinv;
         if (!(ctx->gexec && k == ctx->gkey)) {
             drop_graph(ctx);
             cudaGraph_t g = nullptr;
@@ -1265,6 +1296,7 @@ evc_ctx* evc::clone_context(const evc_ctx* src)
     c->sten_groups = src->sten_groups;
     c->method = src->method;
     c->shared_krylov = src->shared_krylov;
+    c->tinv_lanczos = src->tinv_lanczos;
     c->quad_rule = src->quad_rule;
     c->min_steps = src->min_steps;
     c->probe_offset = src->probe_offset;
@@ -1705,6 +1737,13 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
     if (option == EVC_OPT_SHARED_KRYLOV) {
         if (value != 0 && value != 1) return fail(ctx, EVC_EINVAL, "shared Krylov option must be 0 or 1");
         ctx->shared_krylov = (int)value;
+        ++ctx->prec_version;
+        drop_graph(ctx);
+        return EVC_OK;
+    }
+    if (option == EVC_OPT_TINV_LANCZOS) {
+        if (value != 0 && value != 1) return fail(ctx, EVC_EINVAL, "T^-1 Lanczos option must be 0 or 1");
+        ctx->tinv_lanczos = (int)value;
         ++ctx->prec_version;
         drop_graph(ctx);
         return EVC_OK;

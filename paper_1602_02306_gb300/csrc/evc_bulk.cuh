@@ -71,6 +71,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     return mbar_wait_for(bar, parity, kWaitCycles);
 }
 
+// The same wait taken by all 32 lanes of a warp with one outcome: a lane that
+// gave up makes the whole warp give up, so the lanes never split at a
+// following __syncwarp or shuffle.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity)
+{
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity));
+}
+
 // bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned
 // shared dst; completion counted on bar as transaction bytes.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)

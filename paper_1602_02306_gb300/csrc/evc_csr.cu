@@ -1,7 +1,10 @@
 // evc_csr.cu -- the preconditioned shifted operator for a CSR matrix,
 //   w = M (A - sigma_c I) M q_i - beta_i q_{i-1}       (Algorithm 1, first
 // line of the loop body), with M = I or the Jacobi scaling
-// M = diag((|a_rr - sigma| + eps)^(-1/2)) fused as row and column scales.
+// M = diag((|a_rr - sigma| + eps)^(-1/2)) fused as row and column scales;
+// or, for the T^{-1}-inner-product process (Sec. 4, Eq. lanT1) with T = M^2,
+//   w = T (A - sigma_c I) y_i - beta_i y_{i-1},
+// where T is a row scale only and the gathered rows are not scaled.
 //
 // Row r of C x is  m_r sum_{j != r} a_rj m_j x_j  +  d_r x_r  with the
 // diagonal d_r = (a_rr - sigma) m_r^2 (or a_rr - sigma without M) taken from
@@ -64,11 +67,14 @@ __device__ __forceinline__ Pack<T> ldg16(const T* p)
 // have similar lengths; each group broadcasts the row's (col, val) pairs from
 // its own lanes with warp shuffles.  UNI: every chunk's 32 columns belong to
 // one shift (m a multiple of 32, or one shift), so a gathered entry needs one
-// Jacobi scale, not one per column.
-template <typename T, bool JAC, bool UNI, int NT>
+// Jacobi scale, not one per column.  PM: PM_NONE, PM_JACOBI (row and column
+// scales m) or PM_TLEFT (row scale T = m^2 only; jac then holds m^2).
+template <typename T, int PM, bool UNI, int NT>
 __global__ void __launch_bounds__(NT)
 csr_pass_kernel(CArgs a)
 {
+    constexpr bool JAC = PM == PM_JACOBI;       // gathered rows scaled by m
+    constexpr bool ROWS = PM != PM_NONE;        // output rows scaled
     constexpr int W = 16 / sizeof(T);
     constexpr int LPR = CW / W;                 // lanes per row
     constexpr int RPW = 32 / LPR;               // rows per warp
@@ -87,7 +93,7 @@ csr_pass_kernel(CArgs a)
     const T* jr[NJ];
 #pragma unroll
     for (int w = 0; w < NJ; ++w)
-        jr[w] = JAC ? static_cast<const T*>(a.jac) + (int64_t)a.shift_of[c0 + w] * n : nullptr;
+        jr[w] = ROWS ? static_cast<const T*>(a.jac) + (int64_t)a.shift_of[c0 + w] * n : nullptr;
 
     const int64_t beg = valid ? a.op.row_ptr[row] : 0, end = valid ? a.op.row_ptr[row + 1] : 0;
     // the warp walks the longest of its rows; shorter rows contribute zeros
@@ -152,7 +158,7 @@ csr_pass_kernel(CArgs a)
     for (int w = 0; w < W; ++w) {
         const int c = c0 + w;
         T r = acc[w];
-        if (JAC) r = mul_rn(r, __ldg(jr[UNI ? 0 : w] + row));
+        if (ROWS) r = mul_rn(r, __ldg(jr[UNI ? 0 : w] + row));
         r = fma_rn(__ldg(dsh + (int64_t)a.shift_of[c] * n + row), cen.v[w], r);
         r = mul_rn(r, (T)a.insc[c]);
         if (pp) r = fma_rn(-(T)a.ppc[c], prev.v[w], r);
@@ -167,7 +173,7 @@ csr_pass_kernel(CArgs a)
 }  // namespace
 
 template <typename T>
-cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, cudaStream_t st)
+cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, int pmode, cudaStream_t st)
 {
     // step i reads slot i-1 (q_i), slot i-2 (q_{i-1}) and writes slot i
     CArgs a;
@@ -191,29 +197,33 @@ cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, c
     // every chunk's columns share one shift when m is a multiple of 32 (the
     // padding columns of the last chunk take the last shift) or S = 1
     const bool uni = r.S == 1 || r.m % CW == 0;
-    auto go = [&](auto jac_t, auto uni_t, auto nt_t) {
-        csr_pass_kernel<T, decltype(jac_t)::value, decltype(uni_t)::value, decltype(nt_t)::value>
+    auto go = [&](auto pm_t, auto uni_t, auto nt_t) {
+        csr_pass_kernel<T, decltype(pm_t)::value, decltype(uni_t)::value, decltype(nt_t)::value>
             <<<grid, decltype(nt_t)::value, 0, st>>>(a);
     };
     using F = std::false_type;
     using Tr = std::true_type;
-    auto by_nt = [&](auto jac_t, auto uni_t) -> bool {
+    auto by_nt = [&](auto pm_t, auto uni_t) -> bool {
         switch (nt) {
-        case 128: go(jac_t, uni_t, std::integral_constant<int, 128>()); return true;
-        case 256: go(jac_t, uni_t, std::integral_constant<int, 256>()); return true;
-        case 512: go(jac_t, uni_t, std::integral_constant<int, 512>()); return true;
+        case 128: go(pm_t, uni_t, std::integral_constant<int, 128>()); return true;
+        case 256: go(pm_t, uni_t, std::integral_constant<int, 256>()); return true;
+        case 512: go(pm_t, uni_t, std::integral_constant<int, 512>()); return true;
         default: return false;
         }
     };
+    using PNone = std::integral_constant<int, PM_NONE>;
+    using PJac = std::integral_constant<int, PM_JACOBI>;
+    using PTl = std::integral_constant<int, PM_TLEFT>;
     bool ok;
-    if (!jacobi) ok = by_nt(F(), F());
-    else if (uni) ok = by_nt(Tr(), Tr());
-    else ok = by_nt(Tr(), F());
+    if (pmode == PM_NONE) ok = by_nt(PNone(), F());
+    else if (pmode == PM_JACOBI) ok = uni ? by_nt(PJac(), Tr()) : by_nt(PJac(), F());
+    else if (pmode == PM_TLEFT) ok = uni ? by_nt(PTl(), Tr()) : by_nt(PTl(), F());
+    else ok = false;
     if (!ok) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-template cudaError_t launch_csr_pass<float>(const CsrOp&, const Run&, int, bool, cudaStream_t);
-template cudaError_t launch_csr_pass<double>(const CsrOp&, const Run&, int, bool, cudaStream_t);
+template cudaError_t launch_csr_pass<float>(const CsrOp&, const Run&, int, int, cudaStream_t);
+template cudaError_t launch_csr_pass<double>(const CsrOp&, const Run&, int, int, cudaStream_t);
 
 }  // namespace evc

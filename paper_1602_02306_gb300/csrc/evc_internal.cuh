@@ -107,10 +107,16 @@ struct Run {
     double* hbuf;            // [kmax][ncol]  h_j = q_j . w of the current step
     double* gram;            // [kmax(kmax+1)/2][ncol]  G_ab = q_a . q_b, a >= b
     double* part_nrm;        // [nchunk][nblk][CW]
-    void* jac;               // T[Sop][n]  (Jacobi scales, when used)
+    void* jac;               // T[Sop][n]  Jacobi scales m_r (or m_r^2 = T in T^{-1} mode)
     void* dsh;               // T[Sop][n]  CSR contexts: the diagonal of the shifted operator,
                              //   (a_rr - sigma) m_r^2 (Lanczos with Jacobi) or a_rr - sigma,
                              //   formed in FP64 from the FP64 diagonal, then rounded
+    // T^{-1}-inner-product Lanczos (Sec. 4, Eq. lanT1) with the Jacobi T = M^2:
+    // the basis holds y_j = M q_j, the operator is T (A - sigma I), and every
+    // inner product of the reorthogonalisation and the norm carry the weight
+    // T^{-1} = diag(|a_rr - sigma| + eps), kept in tinvd.
+    int tinv;
+    void* tinvd;             // T[Sop][n]  T^{-1} diagonal (tinv only)
     // device scalars, rewritten before each replay
     uint64_t* seed;          // [1]
     double breakdown_rel;
@@ -179,21 +185,27 @@ inline int reorth_max_blocks(int64_t n)
 }
 
 // Kernel launchers (T = float for EVC_MIXED, double for EVC_FP64).
+// Diagonal preconditioning of an operator pass: none, M (A - sigma I) M with
+// the Jacobi M, or T (A - sigma I) with T = M^2 (T^{-1}-inner-product mode).
+enum { PM_NONE = 0, PM_JACOBI = 1, PM_TLEFT = 2 };
+
 template <typename T>
 cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const StencilPass& p,
-                                bool jacobi, cudaStream_t st);
+                                int pmode, cudaStream_t st);
 // Arnoldi-type estimator (evc_arnoldi.cu)
 template <typename T>
 cudaError_t launch_row_scale(const Run& r, void* w, int64_t cs, cudaStream_t st);
 cudaError_t launch_arnoldi_quad(const Run& r, int i, cudaStream_t st);
 template <typename T>
-cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, bool jacobi, cudaStream_t st);
+cudaError_t launch_csr_pass(const CsrOp& op, const Run& r, int i, int pmode, cudaStream_t st);
 cudaError_t launch_init_state(const Run& r, cudaStream_t st);
 template <typename T>
 cudaError_t launch_init_probe(const Run& r, cudaStream_t st);
+// form: PM_NONE (m_r and a_rr - sigma), PM_JACOBI (m_r and (a_rr - sigma) m_r^2)
+// or PM_TLEFT (m_r^2, (a_rr - sigma) m_r^2 and the T^{-1} diagonal).
 template <typename T>
 cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V, double vdiag,
-                                 double eps, bool jac_form, cudaStream_t st);
+                                 double eps, int form, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st);
 template <typename T>

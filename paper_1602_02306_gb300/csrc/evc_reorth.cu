@@ -12,6 +12,12 @@
 //           beta_{i+1} = ||w||, s_{i+1} = 1/beta_{i+1} and the breakdown test
 //   finish  eig(J_i) -> quadrature, per-shift mean L(i) and stop rule
 //           (every step under a tolerance, else once after the last step).
+// T^{-1}-inner-product mode (Sec. 4, Eq. lanT1, Jacobi T = M^2): the basis
+// holds y_j = M q_j, w = T (A - sigma I) y_i - beta_i y_{i-1}, and every inner
+// product above is <x, y> = x^T T^{-1} y -- the dot kernel weights w and y_i
+// by T^{-1} on load, the update kernel weights the norm -- so the same
+// coefficients, Gram matrix and J_i come out (Y_i = M Q_i).
+//
 // In exact arithmetic G = I, c = h, and the single fused classical
 // Gram-Schmidt sweep equals Algorithm 1's "alpha_i = q_i^T w;
 // w -= alpha_i q_i; w -= Q_i (Q_i^T w)" (the second projection's i-th
@@ -49,13 +55,20 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z)
     return z ^ (z >> 31);
 }
 
+// Correctly rounded square roots in the working precision (an FP64 root per
+// element would make the FP32 probe set-up FP64-bound).
+__device__ __forceinline__ float sqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ double sqrt_rn(double x) { return __dsqrt_rn(x); }
+
 template <typename T>
 __global__ void init_probe_kernel(Run r)
 {
-    // slot 0 of every chunk: the Rademacher probe v (Sec. 2, Eq. trace)
+    // slot 0 of every chunk: the Rademacher probe v (Sec. 2, Eq. trace); in
+    // T^{-1} mode M v (y_1 = M q_1, Sec. 4), m = sqrt of the stored T = m^2
     const uint64_t seed = *r.seed;
     const int64_t total = (int64_t)r.nchunk * r.n * CW;
     T* basis = static_cast<T*>(r.basis);
+    const T* tdiag = static_cast<const T*>(r.jac);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int lane = (int)(e % CW);
@@ -64,7 +77,9 @@ __global__ void init_probe_kernel(Run r)
         const int c = ch * CW + lane;
         const uint64_t j = (uint64_t)r.probe_id[c];
         const uint64_t xh = mix64(seed ^ mix64((j << 32) | (uint64_t)row));
-        basis[ch * r.chunk_stride + row * CW + lane] = (xh >> 63) ? (T)-1 : (T)1;
+        T v = (xh >> 63) ? (T)-1 : (T)1;
+        if (r.tinv) v *= sqrt_rn(tdiag[(int64_t)r.shift_of[c] * r.n + row]);
+        basis[ch * r.chunk_stride + row * CW + lane] = v;
     }
 }
 
@@ -99,16 +114,19 @@ __global__ void init_state_kernel(Run r)
 
 template <typename T>
 __global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, double vdiag, double eps,
-                                    int jac_form)
+                                    int form)
 {
     // M = diag((|a_rr - tau| + eps)^(-1/2)) per shift, and (CSR) the diagonal
-    // of the shifted operator: (a_rr - tau) m_r^2 when M scales it, else
-    // a_rr - tau.  Both from the FP64 diagonal, rounded once at the end: near
-    // a_rr = tau, m_r^2 = 1/(|a_rr - tau| + eps) amplifies an error in a_rr
-    // by up to 1/eps, so neither may be formed from rounded values.
+    // of the shifted operator: (a_rr - tau) m_r^2 when M or T = M^2 scales it,
+    // else a_rr - tau.  In T^{-1} mode (form PM_TLEFT) jac holds T = m_r^2 and
+    // tinvd T^{-1} = |a_rr - tau| + eps.  All from the FP64 diagonal, rounded
+    // once at the end: near a_rr = tau, m_r^2 = 1/(|a_rr - tau| + eps)
+    // amplifies an error in a_rr by up to 1/eps, so none may be formed from
+    // rounded values.
     const int64_t total = (int64_t)r.Sop * r.n;
     T* jac = static_cast<T*>(r.jac);
     T* dsh = static_cast<T*>(r.dsh);
+    T* tinvd = static_cast<T*>(r.tinvd);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(e / r.n);
@@ -116,8 +134,9 @@ __global__ void jacobi_scale_kernel(Run r, const double* diag, const T* V, doubl
         const double d = diag ? diag[row] : (double)V[row] + vdiag;
         const double x = d - r.opshift[s];
         const double m2 = 1.0 / (fabs(x) + eps);
-        if (jac) jac[e] = (T)sqrt(m2);
-        if (dsh) dsh[e] = (T)(jac_form ? x * m2 : x);
+        if (jac) jac[e] = (T)(form == PM_TLEFT ? m2 : sqrt(m2));
+        if (dsh) dsh[e] = (T)(form != PM_NONE ? x * m2 : x);
+        if (tinvd) tinvd[e] = (T)(fabs(x) + eps);
     }
 }
 
@@ -179,7 +198,7 @@ static_assert(UNS % NPROD == 0, "a stage of the update ring must have one produc
 // Each consumer warp has its own ring of NSW stages, so the item a warp
 // waits for is always one phase ahead of the previous item in that stage,
 // which the same warp consumed (mbarrier parities cannot alias).
-template <typename T>
+template <typename T, bool TW>
 __global__ void __launch_bounds__(DTHREADS, 2)
 reorth_dots_kernel(Run r, int i)
 {
@@ -204,6 +223,14 @@ reorth_dots_kernel(Run r, int i)
     const T* q = P + (int64_t)(i - 1) * r.slot_stride;
     const void* lo = P;                                  // this chunk's basis
     const void* hi = P + r.chunk_stride;
+    // T^{-1} weights of this lane's column (TW: T^{-1}-inner-product mode);
+    // when the chunk's columns share one shift, lane l loads row l of the
+    // tile and the others take it by shuffle (one load per tile, not TR)
+    const T* wt = TW ? static_cast<const T*>(r.tinvd) +
+                           (int64_t)r.shift_of[ch * CW + (threadIdx.x & 31)] * r.n
+                     : nullptr;
+    const bool wuni = r.S == 1 || r.m % CW == 0;
+    static_assert(TR <= 32, "one weight per lane covers a tile");
     if (threadIdx.x == 0) {
         for (int s = 0; s < DNS; ++s) {
             mbar_init(&full[s], 1);
@@ -270,12 +297,20 @@ reorth_dots_kernel(Run r, int i)
             const int64_t row0 = r0 + (int64_t)t * TR;
             const int rows = (int)min((int64_t)TR, r1 - row0);
             const int b = t & 1;
-            if (!(ok = mbar_wait(&wqfull[b], (t >> 1) & 1))) break;
+            if (!(ok = mbar_wait_warp(&wqfull[b], (t >> 1) & 1))) break;
             T wv[TR], qv[TR];
+            T dl = 0;
+            if (TW && wuni && lane < rows) dl = __ldg(wt + row0 + lane);
 #pragma unroll
             for (int rr = 0; rr < TR; ++rr) {
                 wv[rr] = rr < rows ? wq[(size_t)(2 * b) * TR * CW + rr * CW + lane] : (T)0;
                 qv[rr] = rr < rows ? wq[(size_t)(2 * b + 1) * TR * CW + rr * CW + lane] : (T)0;
+                if (TW) {
+                    T d = __shfl_sync(0xffffffffu, dl, rr);
+                    if (!wuni && rr < rows) d = __ldg(wt + row0 + rr);
+                    wv[rr] *= d;
+                    qv[rr] *= d;
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&wqempty[b]);
@@ -283,7 +318,7 @@ reorth_dots_kernel(Run r, int i)
             for (int j = warp; j < i; j += CWARPS) {
                 const int64_t k = (int64_t)t * per + j / CWARPS;
                 const int s = warp * NSW + (int)(k % NSW);
-                if (!(ok = mbar_wait(&full[s], (k / NSW) & 1))) break;
+                if (!(ok = mbar_wait_warp(&full[s], (k / NSW) & 1))) break;
                 const T* st = stage + (size_t)s * TR * CW + lane;
                 RTy a = 0, g = 0;
 #pragma unroll
@@ -379,7 +414,7 @@ __global__ void reorth_coef_kernel(Run r, int i)
 // The producer streams, per row tile, the w tile and then every P_j tile;
 // consumer warp q owns rows q*RPW.. of the tile in registers and applies
 // every P_j stage to them, then writes the tile back.
-template <typename T>
+template <typename T, bool TW>
 __global__ void __launch_bounds__(UTHREADS, 2)
 reorth_update_kernel(Run r, int i)
 {
@@ -408,6 +443,12 @@ reorth_update_kernel(Run r, int i)
     T* w = static_cast<T*>(r.basis) + ch * r.chunk_stride + (int64_t)i * r.slot_stride;
     const void* lo = P;
     const void* hi = P + r.chunk_stride;
+    // T^{-1} weights of this lane's column (TW: the norm is <w, w> in T^{-1});
+    // one load per row per warp and shuffles when the chunk has one shift
+    const T* wt = TW ? static_cast<const T*>(r.tinvd) +
+                           (int64_t)r.shift_of[ch * CW + (threadIdx.x & 31)] * r.n
+                     : nullptr;
+    const bool wuni = r.S == 1 || r.m % CW == 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < UNS; ++s) {
             mbar_init(&full[s], 1);
@@ -470,7 +511,7 @@ reorth_update_kernel(Run r, int i)
             const int64_t row0 = r0 + (int64_t)t * TR;
             const int rows = (int)min((int64_t)TR, r1 - row0);
             const int b = t & 1;
-            if (!(ok = mbar_wait(&wfull[b], (t >> 1) & 1))) break;
+            if (!(ok = mbar_wait_warp(&wfull[b], (t >> 1) & 1))) break;
             T wv[RPW];
 #pragma unroll
             for (int rr = 0; rr < RPW; ++rr) {
@@ -481,7 +522,7 @@ reorth_update_kernel(Run r, int i)
             if (lane == 0) mbar_arrive(&wempty[b]);
             for (int j = 0; j < i; ++j, ++item) {
                 const int s = (int)(item % UNS);
-                if (!(ok = mbar_wait(&full[s], (item / UNS) & 1))) break;
+                if (!(ok = mbar_wait_warp(&full[s], (item / UNS) & 1))) break;
                 const T gj = gs[j * CW + lane];
                 const T* st = stage + (size_t)s * TR * CW + (size_t)warp * RPW * CW + lane;
 #pragma unroll
@@ -492,16 +533,23 @@ reorth_update_kernel(Run r, int i)
             }
             if (!ok) break;
             RTy nr = 0;
+            T dl = 0;
+            if (TW && wuni && lane < RPW && warp * RPW + lane < rows)
+                dl = __ldg(wt + row0 + warp * RPW + lane);
 #pragma unroll
             for (int rr = 0; rr < RPW; ++rr) {
                 const int row = warp * RPW + rr;
+                T d = 0;
+                if (TW) d = __shfl_sync(0xffffffffu, dl, rr);
                 if (row < rows) {
                     // BF16 storage of the basis (an accuracy trial): the vector
                     // kept is the rounded one, and beta is its norm
                     if (sizeof(T) == 4 && r.basis_bf16)
                         wv[rr] = (T)__bfloat162float(__float2bfloat16_rn((float)wv[rr]));
                     w[(row0 + row) * CW + lane] = wv[rr];
-                    nr += (RTy)wv[rr] * (RTy)wv[rr];
+                    if (TW && !wuni) d = __ldg(wt + row0 + row);
+                    if (TW) nr += (RTy)(wv[rr] * d) * (RTy)wv[rr];
+                    else nr += (RTy)wv[rr] * (RTy)wv[rr];
                 }
             }
             acc += (double)nr;
@@ -710,12 +758,13 @@ cudaError_t launch_init_probe(const Run& r, cudaStream_t st)
 
 template <typename T>
 cudaError_t launch_jacobi_scales(const Run& r, const double* diag, const void* V, double vdiag,
-                                 double eps, bool jac_form, cudaStream_t st)
+                                 double eps, int form, cudaStream_t st)
 {
     const int64_t total = (int64_t)r.Sop * r.n;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if ((form == PM_TLEFT) != (r.tinv != 0)) return cudaErrorInvalidValue;
     jacobi_scale_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(r, diag, static_cast<const T*>(V),
-                                                             vdiag, eps, jac_form ? 1 : 0);
+                                                             vdiag, eps, form);
     return cudaGetLastError();
 }
 
@@ -733,14 +782,20 @@ size_t update_smem(int i)
            (2 * UNS + 4) * sizeof(uint64_t);
 }
 
+template <typename T, bool TW>
+cudaError_t launch_dots_w(const Run& r, int i, cudaStream_t st)
+{
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = smem_limit_once(attr, reorth_dots_kernel<T, TW>, dots_smem<T>(kMaxSteps));
+    if (e != cudaSuccess) return e;
+    reorth_dots_kernel<T, TW><<<dim3(r.nblk, r.nchunk), DTHREADS, dots_smem<T>(i), st>>>(r, i);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_dots(const Run& r, int i, cudaStream_t st)
 {
-    static std::atomic<uint64_t> attr{0};
-    const cudaError_t e = smem_limit_once(attr, reorth_dots_kernel<T>, dots_smem<T>(kMaxSteps));
-    if (e != cudaSuccess) return e;
-    reorth_dots_kernel<T><<<dim3(r.nblk, r.nchunk), DTHREADS, dots_smem<T>(i), st>>>(r, i);
-    return cudaGetLastError();
+    return r.tinv ? launch_dots_w<T, true>(r, i, st) : launch_dots_w<T, false>(r, i, st);
 }
 
 cudaError_t launch_reduce(const Run& r, int i, cudaStream_t st)
@@ -756,14 +811,21 @@ cudaError_t launch_coef(const Run& r, int i, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename T, bool TW>
+cudaError_t launch_update_w(const Run& r, int i, cudaStream_t st)
+{
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e =
+        smem_limit_once(attr, reorth_update_kernel<T, TW>, update_smem<T>(kMaxSteps));
+    if (e != cudaSuccess) return e;
+    reorth_update_kernel<T, TW><<<dim3(r.nblk, r.nchunk), UTHREADS, update_smem<T>(i), st>>>(r, i);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_update(const Run& r, int i, cudaStream_t st)
 {
-    static std::atomic<uint64_t> attr{0};
-    const cudaError_t e = smem_limit_once(attr, reorth_update_kernel<T>, update_smem<T>(kMaxSteps));
-    if (e != cudaSuccess) return e;
-    reorth_update_kernel<T><<<dim3(r.nblk, r.nchunk), UTHREADS, update_smem<T>(i), st>>>(r, i);
-    return cudaGetLastError();
+    return r.tinv ? launch_update_w<T, true>(r, i, st) : launch_update_w<T, false>(r, i, st);
 }
 
 cudaError_t launch_finish(const Run& r, int i, cudaStream_t st)
@@ -798,9 +860,9 @@ cudaError_t launch_active(const Run& r, int i, cudaStream_t st)
 template cudaError_t launch_init_probe<float>(const Run&, cudaStream_t);
 template cudaError_t launch_init_probe<double>(const Run&, cudaStream_t);
 template cudaError_t launch_jacobi_scales<float>(const Run&, const double*, const void*, double,
-                                                 double, bool, cudaStream_t);
+                                                 double, int, cudaStream_t);
 template cudaError_t launch_jacobi_scales<double>(const Run&, const double*, const void*, double,
-                                                  double, bool, cudaStream_t);
+                                                  double, int, cudaStream_t);
 template cudaError_t launch_dots<float>(const Run&, int, cudaStream_t);
 template cudaError_t launch_dots<double>(const Run&, int, cudaStream_t);
 template cudaError_t launch_update<float>(const Run&, int, cudaStream_t);

@@ -5,7 +5,8 @@
 //   * the Clenshaw steps of the Chebyshev preconditioner M = p_d(K)
 //     (Sec. 6, kinetic-energy preconditioning),
 //   * the shifted Hamiltonian (H - sigma_c I) with a per-column shift,
-//   * the Jacobi-scaled operator diag(m) (H - sigma I) diag(m),
+//   * the Jacobi-scaled operator diag(m) (H - sigma I) diag(m), or
+//     diag(m^2) (H - sigma I) for the T^{-1}-inner-product process (Eq. lanT1),
 //   * and the closing term "- beta_i q_{i-1}" of Algorithm 1.
 //
 // Layout: X[chunk][p][32] with p = x + N*(y + N*z).  Each thread owns one
@@ -84,10 +85,12 @@ struct KArgs {
 // neither instructions nor registers.
 enum { HAS_X = 1, HAS_PREV = 2, HAS_PP = 4, HAS_VS = 8 };
 
-template <typename T, int R, bool JAC, int MASK>
+template <typename T, int R, int PM, int MASK>
 __global__ void __launch_bounds__(STH)
 stencil_pass_kernel(KArgs a)
 {
+    constexpr bool JAC = PM == PM_JACOBI;    // operand scaled by m on load
+    constexpr bool ROWS = PM != PM_NONE;     // output scaled (m, or m^2 = T)
     constexpr int W = 16 / sizeof(T);        // columns per thread
     constexpr int LPP = CW / W;              // threads per grid point
     constexpr int TX = 8;                    // points per block along x
@@ -111,7 +114,7 @@ stencil_pass_kernel(KArgs a)
         s_insc[l].v[w] = a.p.insc ? (T)a.p.insc[c] : (T)1;
         s_a0s[l].v[w] = (T)(a.p.a0 * (a.p.xs ? a.p.xs[c] : 1.0));
         s_ppc[l].v[w] = PP ? (T)a.p.ppc[c] : (T)0;
-        s_shift[threadIdx.x] = JAC ? a.shift_of[c] : 0;
+        s_shift[threadIdx.x] = ROWS ? a.shift_of[c] : 0;
     }
     __syncthreads();
     const int N = a.op.N;
@@ -218,7 +221,7 @@ stencil_pass_kernel(KArgs a)
         }
         const T vp = VS ? __ldg(V + p) : (T)0;
         T mp[W];
-        if (JAC) {
+        if (ROWS) {
 #pragma unroll
             for (int w = 0; w < W; ++w) mp[w] = __ldg(jac + (int64_t)s_shift[sbase + w] * n + p);
         }
@@ -232,7 +235,7 @@ stencil_pass_kernel(KArgs a)
                 off += c2 * (nb[4 % (4 * R)].v[w] + nb[5 % (4 * R)].v[w] + nb[6 % (4 * R)].v[w] +
                              nb[7 % (4 * R)].v[w] + win[0].v[w] + win[2 * R].v[w]);
             T st = k1 * off + (dg + vp - sig.v[w]) * win[R].v[w];
-            if (JAC) st *= mp[w];
+            if (ROWS) st *= mp[w];
             res.v[w] = insc.v[w] * st;
         }
         if (X) {
@@ -537,29 +540,43 @@ constexpr int stencil_loads()
            ((MASK & HAS_PP) ? 1 : 0);
 }
 
-template <typename T, int R, bool JAC, int MASK>
+template <typename T, int R, int PM, int MASK>
 void launch_one(dim3 grid, cudaStream_t st, const KArgs& a)
 {
     constexpr size_t smem = (size_t)(DEPTH + 1) * stencil_loads<R, MASK>() * STH * 16;
     static std::atomic<uint64_t> attr{0};
-    smem_limit_once(attr, stencil_pass_kernel<T, R, JAC, MASK>, smem);
-    stencil_pass_kernel<T, R, JAC, MASK><<<grid, STH, smem, st>>>(a);
+    smem_limit_once(attr, stencil_pass_kernel<T, R, PM, MASK>, smem);
+    stencil_pass_kernel<T, R, PM, MASK><<<grid, STH, smem, st>>>(a);
 }
 
-template <typename T, int R, bool JAC>
+template <typename T, int R, int PM>
 bool launch_masked(int mask, dim3 grid, cudaStream_t st, const KArgs& a)
 {
     switch (mask) {
-    case 0: launch_one<T, R, JAC, 0>(grid, st, a); break;
-    case HAS_X: launch_one<T, R, JAC, HAS_X>(grid, st, a); break;
-    case HAS_X | HAS_PREV: launch_one<T, R, JAC, HAS_X | HAS_PREV>(grid, st, a); break;
-    case HAS_X | HAS_PP: launch_one<T, R, JAC, HAS_X | HAS_PP>(grid, st, a); break;
-    case HAS_X | HAS_PREV | HAS_PP: launch_one<T, R, JAC, HAS_X | HAS_PREV | HAS_PP>(grid, st, a); break;
-    case HAS_PP: launch_one<T, R, JAC, HAS_PP>(grid, st, a); break;
-    case HAS_VS: launch_one<T, R, JAC, HAS_VS>(grid, st, a); break;
-    case HAS_VS | HAS_PP: launch_one<T, R, JAC, HAS_VS | HAS_PP>(grid, st, a); break;
+    case 0: launch_one<T, R, PM, 0>(grid, st, a); break;
+    case HAS_X: launch_one<T, R, PM, HAS_X>(grid, st, a); break;
+    case HAS_X | HAS_PREV: launch_one<T, R, PM, HAS_X | HAS_PREV>(grid, st, a); break;
+    case HAS_X | HAS_PP: launch_one<T, R, PM, HAS_X | HAS_PP>(grid, st, a); break;
+    case HAS_X | HAS_PREV | HAS_PP: launch_one<T, R, PM, HAS_X | HAS_PREV | HAS_PP>(grid, st, a); break;
+    case HAS_PP: launch_one<T, R, PM, HAS_PP>(grid, st, a); break;
+    case HAS_VS: launch_one<T, R, PM, HAS_VS>(grid, st, a); break;
+    case HAS_VS | HAS_PP: launch_one<T, R, PM, HAS_VS | HAS_PP>(grid, st, a); break;
     default:
         return false;   // not an operand set the library issues
+    }
+    return true;
+}
+
+// The operand sets of the diagonally preconditioned passes: the Lanczos step
+// (V and the shift, with or without q_{i-1}).
+template <typename T, int R, int PM>
+bool launch_masked_diag(int mask, dim3 grid, cudaStream_t st, const KArgs& a)
+{
+    switch (mask) {
+    case HAS_VS: launch_one<T, R, PM, HAS_VS>(grid, st, a); break;
+    case HAS_VS | HAS_PP: launch_one<T, R, PM, HAS_VS | HAS_PP>(grid, st, a); break;
+    default:
+        return false;
     }
     return true;
 }
@@ -568,7 +585,7 @@ bool launch_masked(int mask, dim3 grid, cudaStream_t st, const KArgs& a)
 
 template <typename T>
 cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const StencilPass& p,
-                                bool jacobi, cudaStream_t st)
+                                int pmode, cudaStream_t st)
 {
     constexpr int W = 16 / sizeof(T);
     constexpr int LPP = CW / W;
@@ -608,7 +625,7 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |
                      (p.useV ? HAS_VS : 0);
     bool ok;
-    if (!jacobi && op.patch == 2 && N % 2 == 0) {
+    if (pmode == PM_NONE && op.patch == 2 && N % 2 == 0) {
         // 2 x 2 patches: PTW x (2 TYP) points per block
         const int TYP = (op.order == 2 ? patch_threads<1>() : patch_threads<2>()) / LPP / (PTW / 2);
         dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb, cn);
@@ -617,19 +634,24 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
         if (!ok) return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
-    if (op.order == 2)
-        ok = jacobi ? launch_masked<T, 1, true>(mask, grid, st, a)
-                    : launch_masked<T, 1, false>(mask, grid, st, a);
+    if (pmode == PM_NONE)
+        ok = op.order == 2 ? launch_masked<T, 1, PM_NONE>(mask, grid, st, a)
+                           : launch_masked<T, 2, PM_NONE>(mask, grid, st, a);
+    else if (pmode == PM_JACOBI)
+        ok = op.order == 2 ? launch_masked_diag<T, 1, PM_JACOBI>(mask, grid, st, a)
+                           : launch_masked_diag<T, 2, PM_JACOBI>(mask, grid, st, a);
+    else if (pmode == PM_TLEFT)
+        ok = op.order == 2 ? launch_masked_diag<T, 1, PM_TLEFT>(mask, grid, st, a)
+                           : launch_masked_diag<T, 2, PM_TLEFT>(mask, grid, st, a);
     else
-        ok = jacobi ? launch_masked<T, 2, true>(mask, grid, st, a)
-                    : launch_masked<T, 2, false>(mask, grid, st, a);
+        ok = false;
     if (!ok) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 template cudaError_t launch_stencil_pass<float>(const StencilOp&, const Run&, const StencilPass&,
-                                                bool, cudaStream_t);
+                                                int, cudaStream_t);
 template cudaError_t launch_stencil_pass<double>(const StencilOp&, const Run&, const StencilPass&,
-                                                 bool, cudaStream_t);
+                                                 int, cudaStream_t);
 
 }  // namespace evc

@@ -34,6 +34,7 @@ EVC_OPT_METHOD = 11
 EVC_OPT_STENCIL_PATCH = 12
 EVC_OPT_STENCIL_GROUPS = 13
 EVC_OPT_SHARED_KRYLOV = 14
+EVC_OPT_TINV_LANCZOS = 15
 EVC_METHOD_LANCZOS, EVC_METHOD_ARNOLDI = 0, 1
 EVC_CHEB_FACTORED, EVC_CHEB_CLENSHAW = 0, 1
 EVC_QUAD_GAUSS, EVC_QUAD_GA = 0, 1

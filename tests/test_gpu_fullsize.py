@@ -33,7 +33,7 @@ def _lib():
     evc.load()
 
 
-def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS):
+def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS, tinv=0):
     import torch
     if W.kind == "stencil":
         ctx = evc.Context.stencil(W.N, W.h, W.order, W.potential(), precision=precision)
@@ -49,6 +49,7 @@ def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS):
         ctx.set_precond(kind, *W.prec_params)
         evc.evc_set_option(ctx.h, evc.EVC_OPT_MIN_STEPS, W.min_steps)
         evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, method)
+        evc.evc_set_option(ctx.h, evc.EVC_OPT_TINV_LANCZOS, tinv)
         out = ctx.count_slices(W.shifts, W.nprobe, W.maxsteps, tol=W.tol, seed=0)
     torch.cuda.empty_cache()
     return out
@@ -123,6 +124,22 @@ def test_powerlaw_2m_mixed_estimate_within_half(powerlaw_2m_runs):
     # the stated target: the FP32-mixed estimate within 0.5 of FP64's
     W, (L64, _, _), (Lmx, _, _) = powerlaw_2m_runs
     assert abs((Lmx[-1] - Lmx[0]) - (L64[-1] - L64[0])) < MIXED_TOL
+
+
+def test_powerlaw_2m_tinv_lanczos_fullsize(powerlaw_2m_runs):
+    # the T^{-1}-inner-product process (Sec. 4, Eq. lanT1) on the same
+    # workload: FP64 per probe equal to Algorithm 1's (measured 8.5e-7 on
+    # values near 7e5, 1.2e-12 relative), mixed n_below within 5e-5 relative
+    W, (L64, q64, st64), _ = powerlaw_2m_runs
+    Lt, qt, stt = _gpu(W, evc.EVC_FP64, tinv=1)
+    assert list(stt) == list(st64)
+    np.testing.assert_allclose(qt, q64, rtol=1e-11, atol=FP64_TOL)
+    Ltm, qtm, _ = _gpu(W, evc.EVC_MIXED, tinv=1)
+    np.testing.assert_allclose(Ltm, L64, rtol=5e-5)
+    ids = [0, 77, 127]
+    ref = _sample_oracle(W, _oracle_problem(W), range(len(W.shifts)), ids, st64)
+    for s in range(len(W.shifts)):
+        np.testing.assert_allclose(qtm[s, ids], ref[s], rtol=1e-3)
 
 
 def test_slicing_96_fullsize():

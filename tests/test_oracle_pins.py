@@ -513,3 +513,28 @@ def test_tinv_lanczos_equals_algorithm1_chebyshev_stencil():
     assert k2 == kd
     np.testing.assert_allclose(a2, al, rtol=1e-8, atol=1e-9)
     np.testing.assert_allclose(b2, be, rtol=1e-8, atol=1e-9)
+
+
+def test_tinv_lanczos_equals_algorithm1_jacobi_csr():
+    # the diagonal case: Jacobi T = M^2 = diag(1/(|a_rr - tau| + eps)) on a
+    # sparse indefinite matrix, z_1 = M^{-1} q_1 by division, T^{-1} never
+    # formed; Algorithm 1 runs on the CSR oracle with its own Jacobi M
+    from oracle.lanczos_tinv import lanczos_tinv
+    n, tau, k, eps = 80, 0.4, 16, 1e-3
+    A = I.random_symmetric_dense(n, seed=31)
+    A[np.abs(A) < 1.0] = 0.0
+    A = 0.5 * (A + A.T) + np.diag(np.linspace(-2, 2, n))
+    csr = I.dense_to_csr(A)
+    P = O.Problem.csr_matrix(csr, O.PREC_JACOBI, jac_eps=eps)
+    mdiag = O.apply_M(P, tau, np.ones(n))
+    # the oracle's M is the Jacobi scaling itself
+    np.testing.assert_allclose(mdiag, 1.0 / np.sqrt(np.abs(np.diag(A) - tau) + eps), rtol=1e-14)
+    v = O.probe_vector(3, 2, n)
+    al, be, _, kd = O.lanczos(P, tau, v, k)
+    q1 = v / np.linalg.norm(v)
+    a2, b2, k2 = lanczos_tinv(lambda x: A @ x - tau * x, lambda x: mdiag ** 2 * x, mdiag * q1,
+                              q1 / mdiag, k)
+    assert k2 == kd == k
+    np.testing.assert_allclose(a2, al, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(b2, be, rtol=1e-9, atol=1e-10)
+    assert O.gauss_quad(a2, b2, n) == pytest.approx(O.gauss_quad(al, be, n), abs=1e-9)
