@@ -198,6 +198,13 @@ static_assert(UNS % NPROD == 0, "a stage of the update ring must have one produc
 // Each consumer warp has its own ring of NSW stages, so the item a warp
 // waits for is always one phase ahead of the previous item in that stage,
 // which the same warp consumed (mbarrier parities cannot alias).
+// TW (T^{-1}-inner-product mode): every w and q_i tile is weighted by T^{-1}.
+// FP64: the second producer warp weights each tile in shared memory once it
+// lands (all 32 lanes, one column each) and releases it to the consumers on
+// wqready -- one pass per block and tile, where the FP64 consumer warps have
+// no multiplies to spare.  FP32: each consumer warp weights its register
+// copies (one load and TR shuffles per tile), which keeps the second producer
+// free to issue copies (measured faster for FP32, slower for FP64).
 template <typename T, bool TW>
 __global__ void __launch_bounds__(DTHREADS, 2)
 reorth_dots_kernel(Run r, int i)
@@ -213,6 +220,7 @@ reorth_dots_kernel(Run r, int i)
     uint64_t* empty = full + DNS;
     uint64_t* wqfull = empty + DNS;
     uint64_t* wqempty = wqfull + 2;
+    uint64_t* wqready = wqempty + 2;                     // TW: weighted tiles
     __shared__ int s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t r0, r1;
@@ -231,6 +239,9 @@ reorth_dots_kernel(Run r, int i)
                      : nullptr;
     const bool wuni = r.S == 1 || r.m % CW == 0;
     static_assert(TR <= 32, "one weight per lane covers a tile");
+    static_assert(NPROD >= 2, "the second producer warp weights the tiles");
+    constexpr bool PRODW = TW && sizeof(T) == 8;         // weights applied by a producer warp
+    constexpr bool CONSW = TW && sizeof(T) == 4;         // ... by each consumer warp
     if (threadIdx.x == 0) {
         for (int s = 0; s < DNS; ++s) {
             mbar_init(&full[s], 1);
@@ -239,6 +250,7 @@ reorth_dots_kernel(Run r, int i)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&wqfull[b], 1);
             mbar_init(&wqempty[b], CWARPS);
+            mbar_init(&wqready[b], 32);
         }
         mbar_init_fence();
         s_fail = 0;
@@ -254,7 +266,8 @@ reorth_dots_kernel(Run r, int i)
         // about one copy per quarter microsecond); producer 0 also issues the
         // w and q_i tiles.
         const int pw = warp - CWARPS;
-        if (lane == 0) {
+        const bool weigh = PRODW && pw == 1;     // the whole warp weights the w, q tiles
+        if (lane == 0 || weigh) {
             int64_t lastk[DNS];                  // last item issued into each stage
             int lastt[2] = {-1, -1};             // last tile issued into each w/q buffer
             for (int s = 0; s < DNS; ++s) lastk[s] = -1;
@@ -262,27 +275,53 @@ reorth_dots_kernel(Run r, int i)
                 const int64_t row0 = r0 + (int64_t)t * TR;
                 const uint32_t bytes = (uint32_t)(min((int64_t)TR, r1 - row0) * CW * sizeof(T));
                 const int b = t & 1;
-                if (pw == 0) {
-                    if (t >= 2 && !(ok = mbar_wait(&wqempty[b], ((t >> 1) - 1) & 1))) break;
-                    lastt[b] = t;
-                    mbar_arrive_expect_tx(&wqfull[b], 2 * bytes);
-                    ok = checked_bulk(wq + (size_t)(2 * b) * TR * CW, w + row0 * CW, bytes,
-                                      &wqfull[b], lo, hi, r.err) &&
-                         checked_bulk(wq + (size_t)(2 * b + 1) * TR * CW, q + row0 * CW, bytes,
-                                      &wqfull[b], lo, hi, r.err);
+                if (weigh) {
+                    // w <- T^{-1} w, q_i <- T^{-1} q_i in place, lane = column
+                    if (!(ok = mbar_wait_warp(&wqfull[b], (t >> 1) & 1))) break;
+                    const int rows = (int)min((int64_t)TR, r1 - row0);
+                    T* wtile = wq + (size_t)(2 * b) * TR * CW + lane;
+                    T* qtile = wq + (size_t)(2 * b + 1) * TR * CW + lane;
+                    T dl = 0;
+                    if (wuni && lane < rows) dl = __ldg(wt + row0 + lane);
+#pragma unroll
+                    for (int rr = 0; rr < TR; ++rr) {
+                        T d = __shfl_sync(0xffffffffu, dl, rr);
+                        if (rr < rows) {
+                            if (!wuni) d = __ldg(wt + row0 + rr);
+                            wtile[rr * CW] *= d;
+                            qtile[rr * CW] *= d;
+                        }
+                    }
+                    // the next bulk copy into this buffer must follow these writes
+                    fence_proxy_async_smem();
+                    mbar_arrive(&wqready[b]);
                 }
-                for (int j = pw; j < i && ok; j += NPROD) {
-                    // k-th item of consumer warp cw lives in stage cw*NSW + k % NSW
-                    const int cw = j % CWARPS;
-                    const int64_t k = (int64_t)t * ((i - cw + CWARPS - 1) / CWARPS) + j / CWARPS;
-                    const int s = cw * NSW + (int)(k % NSW);
-                    if (k >= NSW && !(ok = mbar_wait(&empty[s], ((k / NSW) - 1) & 1))) break;
-                    lastk[s] = k;
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    ok = checked_bulk(stage + (size_t)s * TR * CW,
-                                      P + (int64_t)j * r.slot_stride + row0 * CW, bytes, &full[s],
-                                      lo, hi, r.err);
+                if (lane == 0) {
+                    if (pw == 0) {
+                        // (warp 0 runs this loop on lane 0 alone: the break leaves it)
+                        if (t >= 2 && !(ok = mbar_wait(&wqempty[b], ((t >> 1) - 1) & 1))) break;
+                        lastt[b] = t;
+                        mbar_arrive_expect_tx(&wqfull[b], 2 * bytes);
+                        ok = checked_bulk(wq + (size_t)(2 * b) * TR * CW, w + row0 * CW, bytes,
+                                          &wqfull[b], lo, hi, r.err) &&
+                             checked_bulk(wq + (size_t)(2 * b + 1) * TR * CW, q + row0 * CW, bytes,
+                                          &wqfull[b], lo, hi, r.err);
+                    }
+                    for (int j = pw; j < i && ok; j += NPROD) {
+                        // k-th item of consumer warp cw lives in stage cw*NSW + k % NSW
+                        const int cw = j % CWARPS;
+                        const int64_t k = (int64_t)t * ((i - cw + CWARPS - 1) / CWARPS) + j / CWARPS;
+                        const int s = cw * NSW + (int)(k % NSW);
+                        if (k >= NSW && !(ok = mbar_wait(&empty[s], ((k / NSW) - 1) & 1))) break;
+                        lastk[s] = k;
+                        mbar_arrive_expect_tx(&full[s], bytes);
+                        ok = checked_bulk(stage + (size_t)s * TR * CW,
+                                          P + (int64_t)j * r.slot_stride + row0 * CW, bytes,
+                                          &full[s], lo, hi, r.err);
+                    }
                 }
+                // the weighing warp leaves the loop as one
+                if (weigh) ok = __shfl_sync(0xffffffffu, ok, 0);
             }
             if (!ok) {
                 // let the copies already issued land before the block exits
@@ -297,15 +336,15 @@ reorth_dots_kernel(Run r, int i)
             const int64_t row0 = r0 + (int64_t)t * TR;
             const int rows = (int)min((int64_t)TR, r1 - row0);
             const int b = t & 1;
-            if (!(ok = mbar_wait_warp(&wqfull[b], (t >> 1) & 1))) break;
+            if (!(ok = mbar_wait_warp(PRODW ? &wqready[b] : &wqfull[b], (t >> 1) & 1))) break;
             T wv[TR], qv[TR];
             T dl = 0;
-            if (TW && wuni && lane < rows) dl = __ldg(wt + row0 + lane);
+            if (CONSW && wuni && lane < rows) dl = __ldg(wt + row0 + lane);
 #pragma unroll
             for (int rr = 0; rr < TR; ++rr) {
                 wv[rr] = rr < rows ? wq[(size_t)(2 * b) * TR * CW + rr * CW + lane] : (T)0;
                 qv[rr] = rr < rows ? wq[(size_t)(2 * b + 1) * TR * CW + rr * CW + lane] : (T)0;
-                if (TW) {
+                if (CONSW) {
                     T d = __shfl_sync(0xffffffffu, dl, rr);
                     if (!wuni && rr < rows) d = __ldg(wt + row0 + rr);
                     wv[rr] *= d;
@@ -772,7 +811,7 @@ template <typename T>
 size_t dots_smem(int i)
 {
     return (size_t)(DNS + 4) * DSTAGE + (size_t)2 * i * CW * sizeof(double) +
-           (2 * DNS + 4) * sizeof(uint64_t);
+           (2 * DNS + 6) * sizeof(uint64_t);
 }
 
 template <typename T>

@@ -265,7 +265,8 @@ stencil_pass_kernel(KArgs a)
     cp_async_wait<0>();
 }
 
-// Patch variant of the same pass (no Jacobi scaling): each thread owns the
+// Patch variant of the same pass (no operand scaling; PM_TLEFT scales the
+// output rows by T = m^2 for the T^{-1}-inner-product process): each thread owns the
 // same 16-byte column vector of a PX x PY patch of (x, y) points and marches
 // them along z together.  Neighbours that fall inside the patch come from the
 // thread's own register window; only the 2R(PX + PY) points around the patch
@@ -304,10 +305,12 @@ __host__ __device__ constexpr int patch_depth()
     return fit < DMAXP ? fit : DMAXP;
 }
 
-template <typename T, int R, int MASK, int PX, int PY>
+template <typename T, int R, int MASK, int PX, int PY, int PM>
 __global__ void __launch_bounds__(patch_threads<R>())
 stencil_patch_kernel(KArgs a)
 {
+    static_assert(PM == PM_NONE || PM == PM_TLEFT, "the patch pass scales no operand");
+    constexpr bool ROWS = PM == PM_TLEFT;
     constexpr int STP = patch_threads<R>();
     constexpr int DEPTHP = patch_depth<R, MASK, PX, PY>();
     static_assert(DEPTHP >= 1, "patch kernel slots do not fit shared memory");
@@ -328,6 +331,7 @@ stencil_patch_kernel(KArgs a)
     extern __shared__ __align__(16) unsigned char st_raw[];
     Pack<T>* slots = reinterpret_cast<Pack<T>*>(st_raw);      // [DEPTHP+1][NL][STP]
     __shared__ Pack<T> s_sig[LPP], s_insc[LPP], s_a0s[LPP], s_ppc[LPP];
+    __shared__ int s_shift[CW];
     if (threadIdx.x < CW) {
         const int c = ch * CW + threadIdx.x;
         const int l = threadIdx.x / W, w = threadIdx.x % W;
@@ -335,11 +339,14 @@ stencil_patch_kernel(KArgs a)
         s_insc[l].v[w] = a.p.insc ? (T)a.p.insc[c] : (T)1;
         s_a0s[l].v[w] = (T)(a.p.a0 * (a.p.xs ? a.p.xs[c] : 1.0));
         s_ppc[l].v[w] = PP ? (T)a.p.ppc[c] : (T)0;
+        s_shift[threadIdx.x] = ROWS ? a.shift_of[c] : 0;
     }
     __syncthreads();
     const int N = a.op.N;
     const int lane = threadIdx.x % LPP;
     const int pt = threadIdx.x / LPP;
+    const T* __restrict__ jac = static_cast<const T*>(a.jac);
+    const int64_t n = a.n;
     const int tilesX = (N + TXP * PX - 1) / (TXP * PX);
     const int x = (blockIdx.x % tilesX) * (TXP * PX) + (pt % TXP) * PX;
     const int y = (blockIdx.x / tilesX) * (TYP * PY) + (pt / TXP) * PY;
@@ -466,7 +473,9 @@ stencil_patch_kernel(KArgs a)
                     if (R == 2)
                         off += c2 * (nbv(-2, 0).v[w] + nbv(2, 0).v[w] + nbv(0, -2).v[w] +
                                      nbv(0, 2).v[w] + win[0][pp_].v[w] + win[2 * R][pp_].v[w]);
-                    const T stv = k1 * off + (dg + vp - sig.v[w]) * win[R][pp_].v[w];
+                    T stv = k1 * off + (dg + vp - sig.v[w]) * win[R][pp_].v[w];
+                    if (ROWS)
+                        stv *= __ldg(jac + (int64_t)s_shift[lane * W + w] * n + cxy[pp_] + rowz);
                     res.v[w] = insc.v[w] * stv;
                 }
                 int k = 0;
@@ -501,7 +510,7 @@ stencil_patch_kernel(KArgs a)
     cp_async_wait<0>();
 }
 
-template <typename T, int R, int MASK, int PX, int PY>
+template <typename T, int R, int MASK, int PX, int PY, int PM = PM_NONE>
 void launch_patch(dim3 grid, cudaStream_t st, const KArgs& a)
 {
     constexpr int NB = 2 * R * (PX + PY);
@@ -511,8 +520,22 @@ void launch_patch(dim3 grid, cudaStream_t st, const KArgs& a)
         (size_t)(patch_depth<R, MASK, PX, PY>() + 1) * (NB + PX * PY * (1 + NOP)) * STP * 16;
     // a failure here shows as the launch's error
     static std::atomic<uint64_t> attr{0};
-    smem_limit_once(attr, stencil_patch_kernel<T, R, MASK, PX, PY>, smem);
-    stencil_patch_kernel<T, R, MASK, PX, PY><<<grid, STP, smem, st>>>(a);
+    smem_limit_once(attr, stencil_patch_kernel<T, R, MASK, PX, PY, PM>, smem);
+    stencil_patch_kernel<T, R, MASK, PX, PY, PM><<<grid, STP, smem, st>>>(a);
+}
+
+// The operand sets of the T-scaled Lanczos step (V and the shift, with or
+// without q_{i-1}).
+template <typename T, int R, int PX, int PY>
+bool launch_patch_masked_tl(int mask, dim3 grid, cudaStream_t st, const KArgs& a)
+{
+    switch (mask) {
+    case HAS_VS: launch_patch<T, R, HAS_VS, PX, PY, PM_TLEFT>(grid, st, a); break;
+    case HAS_VS | HAS_PP: launch_patch<T, R, HAS_VS | HAS_PP, PX, PY, PM_TLEFT>(grid, st, a); break;
+    default:
+        return false;
+    }
+    return true;
 }
 
 template <typename T, int R, int PX, int PY>
@@ -625,12 +648,16 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |
                      (p.useV ? HAS_VS : 0);
     bool ok;
-    if (pmode == PM_NONE && op.patch == 2 && N % 2 == 0) {
+    if (pmode != PM_JACOBI && op.patch == 2 && N % 2 == 0) {
         // 2 x 2 patches: PTW x (2 TYP) points per block
         const int TYP = (op.order == 2 ? patch_threads<1>() : patch_threads<2>()) / LPP / (PTW / 2);
         dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb, cn);
-        ok = op.order == 2 ? launch_patch_masked<T, 1, 2, 2>(mask, pg, st, a)
-                           : launch_patch_masked<T, 2, 2, 2>(mask, pg, st, a);
+        if (pmode == PM_TLEFT)
+            ok = op.order == 2 ? launch_patch_masked_tl<T, 1, 2, 2>(mask, pg, st, a)
+                               : launch_patch_masked_tl<T, 2, 2, 2>(mask, pg, st, a);
+        else
+            ok = op.order == 2 ? launch_patch_masked<T, 1, 2, 2>(mask, pg, st, a)
+                               : launch_patch_masked<T, 2, 2, 2>(mask, pg, st, a);
         if (!ok) return cudaErrorInvalidValue;
         return cudaGetLastError();
     }

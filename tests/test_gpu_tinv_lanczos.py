@@ -102,14 +102,16 @@ def test_csr_fp64_adaptive_stop_and_ga_rule():
         assert np.max(np.abs(q - qr)) < FP64_TOL
 
 
-@pytest.mark.parametrize("order", [2, 4])
-def test_stencil_fp64_against_the_oracle(order):
+@pytest.mark.parametrize("order,patch", [(2, 1), (4, 1), (2, 2), (4, 2)])
+def test_stencil_fp64_against_the_oracle(order, patch):
+    # per-thread pass and 2 x 2 patch pass (both scale output rows by T)
     N, h = 10, 0.3
     V = I.gaussian_wells(N, h, nwells=4, seed=1)
     shifts, m, k = [-2.0, -0.7], 40, 18
     with evc.Context.stencil(N, h, order, V, precision=evc.EVC_FP64) as ctx:
         ctx.set_precond(evc.EVC_PREC_JACOBI, EPS)
         ctx.set_option(evc.EVC_OPT_TINV_LANCZOS, 1)
+        ctx.set_option(evc.EVC_OPT_STENCIL_PATCH, patch)
         L, q, st = ctx.count_slices(shifts, m, k, seed=2)
     P = O.Problem.stencil(N, h, order, V, O.PREC_JACOBI, jac_eps=EPS)
     qr, _ = _oracle_tinv(P, shifts, m, k, seed=2)
@@ -188,3 +190,21 @@ def test_identity_is_algorithm1_and_unsupported_forms_fail():
         assert e.value.code == evc.EVC_EUNSUPPORTED
         ctx.set_option(evc.EVC_OPT_TINV_LANCZOS, 0)
         ctx.count_slices([-1.0], 32, 10, seed=0)  # the context stays usable
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_stencil_patch_pass_is_bitwise_the_per_thread_pass(order):
+    # mixed precision, chunks that mix shifts (m = 24): the patch kernel's
+    # T-scaled rows equal the per-thread kernel's bit for bit
+    N, h = 12, 0.3
+    V = I.gaussian_wells(N, h, nwells=4, seed=3)
+    shifts, m, k = [-2.2, -1.0, 0.1], 24, 15
+    res = []
+    for patch in (1, 2):
+        with evc.Context.stencil(N, h, order, V, precision=evc.EVC_MIXED) as ctx:
+            ctx.set_precond(evc.EVC_PREC_JACOBI, EPS)
+            ctx.set_option(evc.EVC_OPT_TINV_LANCZOS, 1)
+            ctx.set_option(evc.EVC_OPT_STENCIL_PATCH, patch)
+            res.append(ctx.count_slices(shifts, m, k, seed=6))
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    np.testing.assert_array_equal(res[0][0], res[1][0])
