@@ -375,6 +375,7 @@ def _tinv_leg(evc, ctx, W, stream, seed, steps):
     import torch
     S, m, k = len(W.shifts), W.nprobe, W.maxsteps
     evc.evc_set_option(ctx.h, evc.EVC_OPT_TINV_LANCZOS, 1)
+    ctx.reserve(S, m, k)          # one more per-shift array (the T^{-1} weights)
     dq = torch.empty(S * m, dtype=torch.float64, device="cuda")
     dL = torch.empty(S, dtype=torch.float64, device="cuda")
     ds = torch.empty(S, dtype=torch.int32, device="cuda")
