@@ -317,11 +317,12 @@ def _measure(evc, W, args, stream, peak, peak_kind, steps, warmup, seed, tune=Tr
     evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
     launches = sum(1 for r in recs if not r[4])   # span records are not launches
     # the stencil class runs the patch kernel when the tuner chose 2 x 2 patches
-    # (passes without Jacobi scaling, N even)
+    # (passes without Jacobi scaling, N even), the tiled kernel for patch 3
+    # (N a multiple of its 8 x 8 tile, else the patch kernel)
     sname = "stencil_pass_kernel"
     patch = tuning.get("stencil_patch") if tuning else _SHAPES["patch"]
-    if W.kind == "stencil" and patch == 2 and W.precond != "jacobi" and W.N % 2 == 0:
-        sname = "stencil_patch_kernel"
+    if W.kind == "stencil" and patch in (2, 3) and W.precond != "jacobi" and W.N % 2 == 0:
+        sname = "stencil_tma_kernel" if patch == 3 and W.N % 8 == 0 else "stencil_patch_kernel"
     roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname, W)
     psteps = float(m * int(np.sum(st)))
     return ctx, {"ms": ms, "L": L, "steps_used": st, "quad": q, "clocks": clk, "roofline": roof,
@@ -897,8 +898,8 @@ def main():
     ap.add_argument("--skip-tinv", action="store_true",
                     help="omit the T^-1-inner-product Lanczos leg (Jacobi workloads)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
-    ap.add_argument("--stencil-patch", type=int, default=0, choices=[0, 1, 2],
-                    help="points per thread of the stencil pass (with --no-autotune)")
+    ap.add_argument("--stencil-patch", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="points per thread of the stencil pass: 1, 2 (2x2 patch) or 3 (2x2 patches of tensor-copied tiles) (with --no-autotune)")
     ap.add_argument("--stencil-zb", type=int, default=0,
                     help="z planes per block of the stencil pass (with --no-autotune)")
     ap.add_argument("--stencil-groups", type=int, default=0, choices=[0, 1, 2, 4],

@@ -240,7 +240,13 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
  *                       pass, 1 (default) or 2 = a 2 x 2 patch of (x, y) points
  *                       whose inner neighbours come from registers (fewer loads
  *                       per output; passes without Jacobi scaling and grids
- *                       with N even, else 1 is used).  Results agree to rounding.
+ *                       with N even, else 1 is used), or 3 = the 2 x 2 patches
+ *                       of a block tile (8 x 8 points FP32, 8 x 4 FP64) whose
+ *                       input tile, stencil arms and pointwise operands are
+ *                       staged in shared memory by tiled tensor copies, plane
+ *                       by plane (N a multiple of the tile, else 2 is used).
+ *                       2 and 3 give bitwise the same results; they agree with
+ *                       1 to rounding.
  *   EVC_OPT_STENCIL_GROUPS: stencil contexts: 1 (default) to 4.  The stencil
  *                       passes of each step's operator application run as this
  *                       many groups of column chunks, each group on its own
@@ -353,7 +359,8 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  * the caller's launch shape) with a pair of timing events around every kernel,
  * and keeps, per kernel family, the fastest of
  *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB) times
- *                  points per thread 1 / 2x2 (EVC_OPT_STENCIL_PATCH), then
+ *                  points per thread 1 / 2x2 / 2x2 in tensor-copied tiles
+ *                  (EVC_OPT_STENCIL_PATCH), then
  *                  1 / 2 / 4 concurrent chunk groups (EVC_OPT_STENCIL_GROUPS),
  *   CSR pass:      threads per block 128 / 256 / 512 (EVC_OPT_CSR_THREADS),
  *   reorthogonalisation: rows per block 64 ... 13824 within the allowed
@@ -367,7 +374,7 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  * the GPU, the grid and the batch. */
 typedef struct {
     int stencil_zb;      /* chosen z planes per block (stencil contexts), else 0 */
-    int stencil_patch;   /* chosen points per thread, 1 or 2 (2 x 2 patch), else 0 */
+    int stencil_patch;   /* chosen EVC_OPT_STENCIL_PATCH value 1, 2 or 3 (stencil contexts), else 0 */
     int stencil_groups;  /* chosen concurrent chunk groups (stencil contexts), else 0 */
     int csr_threads;     /* chosen threads per block (CSR contexts), else 0 */
     int reorth_rows;     /* chosen rows per block of the reorthogonalisation */

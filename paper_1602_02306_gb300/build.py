@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libevc.so")
-SOURCES = ["evc_api.cu", "evc_stencil.cu", "evc_csr.cu", "evc_reorth.cu", "evc_arnoldi.cu",
+SOURCES = ["evc_api.cu", "evc_stencil.cu", "evc_stencil_tma.cu", "evc_csr.cu", "evc_reorth.cu", "evc_arnoldi.cu",
            "evc_static.cu", "evc_server.cu", "evc_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1719,7 +1719,8 @@ int evc_set_option(evc_ctx* ctx, int option, int64_t value)
     }
     if (option == EVC_OPT_STENCIL_PATCH) {
         if (ctx->op != OP_STENCIL) return fail(ctx, EVC_EINVAL, "not a stencil context");
-        if (value != 1 && value != 2) return fail(ctx, EVC_EINVAL, "stencil patch must be 1 or 2");
+        if (value != 1 && value != 2 && value != 3)
+            return fail(ctx, EVC_EINVAL, "stencil patch must be 1, 2 or 3");
         ctx->sten.patch = (int)value;
         ++ctx->prec_version;
         drop_graph(ctx);
@@ -1872,8 +1873,11 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
         cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
         double best = 1e300;
         int bz = cand[0], bp = 1;
-        for (int pa : {1, 2}) {
+        for (int pa : {1, 2, 3}) {
             if (pa == 2 && N % 2) continue;
+            if (pa == 3 && !(ctx->precision == EVC_MIXED ? stencil_tma_eligible<float>(N)
+                                                         : stencil_tma_eligible<double>(N)))
+                continue;
             for (int zb : cand) {
                 ctx->sten.zb = zb;
                 ctx->sten.patch = pa;

@@ -192,6 +192,16 @@ enum { PM_NONE = 0, PM_JACOBI = 1, PM_TLEFT = 2 };
 template <typename T>
 cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const StencilPass& p,
                                 int pmode, cudaStream_t st);
+// The same pass on block tiles staged by tensor copies (evc_stencil_tma.cu):
+// N a multiple of the tile (8 x 8 points FP32, 8 x 4 FP64); PM_NONE or
+// PM_TLEFT.  p, shift_of, sigma and chunk_active are already moved to the
+// launch's first chunk; cn chunks.
+template <typename T>
+bool stencil_tma_eligible(int N);
+template <typename T>
+cudaError_t launch_stencil_tma(const StencilOp& op, const StencilPass& p, const int* shift_of,
+                               const double* sigma, const void* jac, const int* chunk_active,
+                               int64_t n, int* err, int cn, int pmode, cudaStream_t st);
 // Arnoldi-type estimator (evc_arnoldi.cu)
 template <typename T>
 cudaError_t launch_row_scale(const Run& r, void* w, int64_t cs, cudaStream_t st);

@@ -648,7 +648,10 @@ cudaError_t launch_stencil_pass(const StencilOp& op, const Run& r, const Stencil
     const int mask = (p.x ? HAS_X : 0) | (p.prev ? HAS_PREV : 0) | (p.pp ? HAS_PP : 0) |
                      (p.useV ? HAS_VS : 0);
     bool ok;
-    if (pmode != PM_JACOBI && op.patch == 2 && N % 2 == 0) {
+    if (pmode != PM_JACOBI && op.patch == 3 && stencil_tma_eligible<T>(N))
+        return launch_stencil_tma<T>(op, a.p, a.shift_of, a.sigma, a.jac, a.chunk_active, a.n, r.err,
+                                     cn, pmode, st);
+    if (pmode != PM_JACOBI && op.patch >= 2 && N % 2 == 0) {
         // 2 x 2 patches: PTW x (2 TYP) points per block
         const int TYP = (op.order == 2 ? patch_threads<1>() : patch_threads<2>()) / LPP / (PTW / 2);
         dim3 pg(((N + PTW - 1) / PTW) * ((N + 2 * TYP - 1) / (2 * TYP)), (N + zb - 1) / zb, cn);
