@@ -361,7 +361,8 @@ int evc_get_profile(evc_ctx* ctx, evc_prof_rec* recs, int cap, int* nrec);
  *   stencil pass:  z planes per block 16 / 32 / 64 (EVC_OPT_STENCIL_ZB) times
  *                  points per thread 1 / 2x2 / 2x2 in tensor-copied tiles
  *                  (EVC_OPT_STENCIL_PATCH), then
- *                  1 / 2 / 4 concurrent chunk groups (EVC_OPT_STENCIL_GROUPS),
+ *                  1 / 2 / 4 concurrent chunk groups (EVC_OPT_STENCIL_GROUPS), and
+ *                  the shapes once more if the groups changed,
  *   CSR pass:      threads per block 128 / 256 / 512 (EVC_OPT_CSR_THREADS),
  *   reorthogonalisation: rows per block 64 ... 13824 within the allowed
  *                  block counts (EVC_OPT_REORTH_ROWS),

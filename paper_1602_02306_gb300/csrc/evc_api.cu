@@ -1871,30 +1871,37 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
         for (int zb : {16, 32, 64}) cand.push_back(std::min(zb, N));
         std::sort(cand.begin(), cand.end());
         cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-        double best = 1e300;
-        int bz = cand[0], bp = 1;
-        for (int pa : {1, 2, 3}) {
-            if (pa == 2 && N % 2) continue;
-            if (pa == 3 && !(ctx->precision == EVC_MIXED ? stencil_tma_eligible<float>(N)
-                                                         : stencil_tma_eligible<double>(N)))
-                continue;
-            for (int zb : cand) {
-                ctx->sten.zb = zb;
-                ctx->sten.patch = pa;
-                double t;
-                if ((rc = measure(1u << EVC_K_STENCIL, t))) return restore(rc);
-                if (t < best) {
-                    best = t;
-                    bz = zb;
-                    bp = pa;
+        // points per thread and z planes per block at the current chunk groups
+        auto tune_shape = [&]() -> int {
+            double best = 1e300;
+            int bz = cand[0], bp = 1;
+            for (int pa : {1, 2, 3}) {
+                if (pa == 2 && N % 2) continue;
+                if (pa == 3 && !(ctx->precision == EVC_MIXED ? stencil_tma_eligible<float>(N)
+                                                             : stencil_tma_eligible<double>(N)))
+                    continue;
+                for (int zb : cand) {
+                    ctx->sten.zb = zb;
+                    ctx->sten.patch = pa;
+                    double t;
+                    const int e = measure(1u << EVC_K_STENCIL, t);
+                    if (e) return e;
+                    if (t < best) {
+                        best = t;
+                        bz = zb;
+                        bp = pa;
+                    }
                 }
             }
-        }
-        ctx->sten.zb = bz;
-        ctx->sten.patch = bp;
+            ctx->sten.zb = bz;
+            ctx->sten.patch = bp;
+            return EVC_OK;
+        };
+        if ((rc = tune_shape())) return restore(rc);
         // concurrent chunk groups of the operator segment (at most one per chunk)
         const int nchunk = (int)(((int64_t)nshift * nprobe + CW - 1) / CW);
-        best = 1e300;
+        const int g0 = ctx->sten_groups;
+        double best = 1e300;
         int bg = 1;
         for (int g : {1, 2, 4}) {
             if (g > 1 && g > nchunk) continue;
@@ -1907,6 +1914,8 @@ int evc_autotune(evc_ctx* ctx, int nshift, int nprobe, int maxsteps, evc_tuning*
             }
         }
         ctx->sten_groups = bg;
+        // the launch shape of a pass changes with the groups: shapes again
+        if (bg != g0 && (rc = tune_shape())) return restore(rc);
     } else {
         double best = 1e300;
         int bt = 256;
