@@ -496,23 +496,24 @@ cudaError_t launch_tma(dim3 grid, cudaStream_t st, const TmaMaps& maps, const Tm
 template <typename T, int R, int PM>
 cudaError_t launch_tma_masked(int mask, dim3 grid, cudaStream_t st, const TmaMaps& m, const TmaArgs& a)
 {
-    if (PM == PM_TLEFT) {
+    if constexpr (PM == PM_TLEFT) {
         switch (mask) {
         case HAS_VS: return launch_tma<T, R, HAS_VS, PM>(grid, st, m, a);
         case HAS_VS | HAS_PP: return launch_tma<T, R, HAS_VS | HAS_PP, PM>(grid, st, m, a);
         default: return cudaErrorInvalidValue;
         }
-    }
-    switch (mask) {
-    case 0: return launch_tma<T, R, 0, PM>(grid, st, m, a);
-    case HAS_X: return launch_tma<T, R, HAS_X, PM>(grid, st, m, a);
-    case HAS_X | HAS_PREV: return launch_tma<T, R, HAS_X | HAS_PREV, PM>(grid, st, m, a);
-    case HAS_X | HAS_PP: return launch_tma<T, R, HAS_X | HAS_PP, PM>(grid, st, m, a);
-    case HAS_X | HAS_PREV | HAS_PP: return launch_tma<T, R, HAS_X | HAS_PREV | HAS_PP, PM>(grid, st, m, a);
-    case HAS_PP: return launch_tma<T, R, HAS_PP, PM>(grid, st, m, a);
-    case HAS_VS: return launch_tma<T, R, HAS_VS, PM>(grid, st, m, a);
-    case HAS_VS | HAS_PP: return launch_tma<T, R, HAS_VS | HAS_PP, PM>(grid, st, m, a);
-    default: return cudaErrorInvalidValue;
+    } else {
+        switch (mask) {
+        case 0: return launch_tma<T, R, 0, PM>(grid, st, m, a);
+        case HAS_X: return launch_tma<T, R, HAS_X, PM>(grid, st, m, a);
+        case HAS_X | HAS_PREV: return launch_tma<T, R, HAS_X | HAS_PREV, PM>(grid, st, m, a);
+        case HAS_X | HAS_PP: return launch_tma<T, R, HAS_X | HAS_PP, PM>(grid, st, m, a);
+        case HAS_X | HAS_PREV | HAS_PP: return launch_tma<T, R, HAS_X | HAS_PREV | HAS_PP, PM>(grid, st, m, a);
+        case HAS_PP: return launch_tma<T, R, HAS_PP, PM>(grid, st, m, a);
+        case HAS_VS: return launch_tma<T, R, HAS_VS, PM>(grid, st, m, a);
+        case HAS_VS | HAS_PP: return launch_tma<T, R, HAS_VS | HAS_PP, PM>(grid, st, m, a);
+        default: return cudaErrorInvalidValue;
+        }
     }
 }
 
