@@ -229,6 +229,27 @@ def ga_quad(alpha, beta, vnorm2):
     return float(_load().evo_ga_quad(alpha.size, _dp(alpha), _dp(beta), vnorm2))
 
 
+def quad_bound_log10(beta, k, vnorm2):
+    """log10 of the computable factor of the Gauss quadrature error bound
+    (Sec. 3, Eq. qbound): after k Lanczos steps from v/||v||,
+        |eps_k| <= N_k * ||v||^2 * beta_2^2 ... beta_{k+1}^2 / (2k)!
+    where N_k bounds |f^(2k)| on an interval holding the spectrum; this
+    returns log10(||v||^2 beta_2^2 ... beta_{k+1}^2 / (2k)!).  beta[i] is
+    beta_{i+1} (beta[0] = beta_1 = 0).  A zero beta_j (j = 2..k+1: the process
+    broke down) makes the rule exact (Proposition 1): -inf."""
+    beta = np.asarray(beta, dtype=np.float64)
+    assert k >= 1 and beta.size >= k + 1
+    s = np.log10(vnorm2)
+    for j in range(2, k + 2):
+        b = beta[j - 1]
+        if not b > 0.0:
+            return -np.inf
+        s += 2.0 * np.log10(b)
+    for i in range(1, 2 * k + 1):        # (2k)!
+        s -= np.log10(i)
+    return float(s)
+
+
 def count(P: Problem, shifts, m, kmax, tol=0.0, seed=0, probe_ids=None,
           breakdown_rel=BREAKDOWN_REL, nthreads=0, rule=0, min_steps=3):
     """Algorithm 2 for every shift: returns (quad[S, m], steps[S], L[S]).

@@ -270,6 +270,55 @@ def test_moments_exact_to_degree_2k_minus_1():
     assert abs(lhs - rhs) > 1e-6 * abs(rhs)       # degree 2k is not exact in general
 
 
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_quad_bound_is_the_error_for_degree_2k(k):
+    # Sec. 3, Eq. qbound: |eps_k| <= N_k ||v||^2 beta_2^2...beta_{k+1}^2 / (2k)!
+    # with N_k >= |f^(2k)|.  For f(x) = x^(2k), f^(2k) = (2k)! and the bound is
+    # attained: the Gauss error is ||v||^2 times the squared norm of the monic
+    # degree-k orthogonal polynomial (it vanishes at the nodes).  So the
+    # oracle's factor times (2k)! must equal v^T C^(2k) v - ||v||^2 e1^T J^(2k) e1.
+    A = I.random_symmetric_dense(25, seed=8)
+    P = O.Problem.dense_matrix(A, O.PREC_JACOBI)
+    tau = -0.1
+    v = O.probe_vector(1, 2, 25)
+    Cm = _dense_C(P, tau)
+    al, be, _, kd = O.lanczos(P, tau, v, k)
+    assert kd == k
+    J = np.diag(al) + np.diag(be[1:k], 1) + np.diag(be[1:k], -1)
+    err = v @ np.linalg.matrix_power(Cm, 2 * k) @ v - 25.0 * np.linalg.matrix_power(J, 2 * k)[0, 0]
+    import math
+    bound = 10.0 ** O.quad_bound_log10(be, k, v @ v) * math.factorial(2 * k)
+    assert err > 0 and bound == pytest.approx(err, rel=1e-7)
+
+
+def test_quad_bound_holds_for_exp_and_is_exact_after_breakdown():
+    # f = exp on C / ||C||: N_k = max e^x on the spectrum; the Gauss error of
+    # v^T e^C v stays below the bound and above a small fraction of it.  After a
+    # breakdown (p distinct eigenvalues, Proposition 1) the factor is -inf.
+    A = I.random_symmetric_dense(30, seed=5)
+    A = A / np.linalg.norm(A, 2)
+    P = O.Problem.dense_matrix(A)
+    v = O.probe_vector(2, 3, 30)
+    w, U = np.linalg.eigh(A)
+    exact = float(v @ (U * np.exp(w)) @ U.T @ v)
+    for k in (2, 3, 4):
+        al, be, _, _ = O.lanczos(P, 0.0, v, k)
+        th, z1 = np.linalg.eigh(np.diag(al) + np.diag(be[1:k], 1) + np.diag(be[1:k], -1))
+        quad = 30.0 * float(np.sum(np.exp(th) * z1[0] ** 2))
+        bound = np.exp(w.max()) * 10.0 ** O.quad_bound_log10(be, k, v @ v)
+        assert abs(exact - quad) <= bound
+        assert abs(exact - quad) >= 1e-3 * bound
+    D = I.random_symmetric_dense(30, seed=4, distinct=[-2.0, -0.5, 0.7, 1.5, 3.0])
+    al, be, _, kd = O.lanczos(O.Problem.dense_matrix(D), 0.0, v, 12)
+    assert kd == 5
+    # beta_{p+1} is at rounding level: the bound collapses ...
+    assert O.quad_bound_log10(be, kd, v @ v) < -25.0
+    # ... and an exact zero makes the rule exact
+    be = be.copy()
+    be[kd] = 0.0
+    assert O.quad_bound_log10(be, kd, v @ v) == -np.inf
+
+
 def test_proposition1_exact_at_p_distinct_eigenvalues():
     # Sec. 3, Proposition 1: with p distinct eigenvalues of C, k = p is exact,
     # and the Lanczos process breaks down at step p.
