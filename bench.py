@@ -314,6 +314,7 @@ def _measure(evc, W, args, stream, peak, peak_kind, steps, warmup, seed, tune=Tr
     # timed region above, whose events see only the whole counts)
     timed(1, 0, profile=True)
     recs = evc.evc_get_profile(ctx.h)
+    qbound = _quad_bound_summary(evc, ctx, W) if not _METHOD[0] else None
     evc.evc_set_option(ctx.h, evc.EVC_OPT_PROFILE, 0)
     launches = sum(1 for r in recs if not r[4])   # span records are not launches
     # the stencil class runs the patch kernel when the tuner chose 2 x 2 patches
@@ -326,6 +327,7 @@ def _measure(evc, W, args, stream, peak, peak_kind, steps, warmup, seed, tune=Tr
     roof, per_kind = _roofline(evc, recs, peak, peak_kind, sname, W)
     psteps = float(m * int(np.sum(st)))
     return ctx, {"ms": ms, "L": L, "steps_used": st, "quad": q, "clocks": clk, "roofline": roof,
+                 "quad_bound": qbound,
                  "kernels": per_kind, "launches": launches, "psteps": psteps, "ws": ws,
                  "tuning": tuning, "kmax": k, "recs": recs}
 
@@ -361,6 +363,19 @@ def _device_time(r, steps):
     return {"count_ms": round(t, 3), "kernels_ms": round(busy, 3),
             "idle_ms": round(t - busy, 3), "idle_frac": round((t - busy) / t, 4),
             "shift_steps_run": done, "shift_steps_max": len(r["steps_used"]) * int(r["kmax"])}
+
+
+def _quad_bound_summary(evc, ctx, W):
+    """Per shift, the median and the largest over probes of the computable
+    factor of the Gauss quadrature error bound (Sec. 3, Eq. qbound) of the last
+    count: log10(||v||^2 beta_2^2 ... beta_{k+1}^2 / (2k)!)."""
+    S, m = len(W.shifts), W.nprobe
+    qb = evc.evc_get_quad_bound(ctx.h, S * m).reshape(S, m)
+    return {"log10_median": [round(float(np.median(x)), 2) for x in qb],
+            "log10_max": [round(float(np.max(x)), 2) for x in qb],
+            "note": "log10(||v||^2 beta_2^2...beta_{k+1}^2/(2k)!) per probe (Eq. qbound): times a bound "
+                    "on the 2k-th derivative of a smooth stand-in for the step function it bounds "
+                    "the quadrature error"}
 
 
 def _barrier():
@@ -605,6 +620,7 @@ def run_ours(args):
         "fp64": {"skipped": fp64_note} if f64 is None else {
             "value": round(world * f64["psteps"] / (f64["ms_per_step"] * 1e-3), 1), "unit": UNIT,
             "ms_per_step": round(f64["ms_per_step"], 3)},
+        "quad_bound": r.get("quad_bound"),
         "estimate": {"mixed": est_mixed, "fp64": est_fp64,
                      # this rank's probes on both paths (the whole count at N = 1)
                      "mixed_minus_fp64": (float(r["L"][-1] - r["L"][0]) - est_fp64)

@@ -191,6 +191,19 @@ int evc_sync(evc_ctx* ctx);
  * sizes implied by the last call's nshift, nprobe and maxsteps.              */
 int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone);
 
+/* The computable factor of the Gauss quadrature error bound of the last call
+ * (Sec. 3, Eq. qbound): per column c = s*nprobe + j, after the column's
+ * k = kdone[c] steps,
+ *     log10_bound[c] = log10( ||v||^2 beta_2^2 ... beta_{k+1}^2 / (2k)! ),
+ * so that |eps_k| <= N_k * 10^log10_bound[c] for every smooth stand-in of the
+ * step function h that agrees with it on the spectrum and the Ritz values,
+ * N_k bounding its 2k-th derivative there (||v||^2 = n for the Rademacher
+ * probes).  -inf when a beta_j is exactly zero (the process broke down: the
+ * rule is exact, Proposition 1); NaN for a column with no steps.  Host array
+ * double[nshift*nprobe] of the last call.  EVC_EUNSUPPORTED after an Arnoldi
+ * call (no tridiagonal).  A diagnostic: the count does not use it.            */
+int evc_get_quad_bound(evc_ctx* ctx, double* log10_bound);
+
 /* Options.
  *   EVC_OPT_GRAPH     : 1 (default) replays the whole multi-step launch
  *                       sequence as one CUDA graph, 0 launches kernels one by one.

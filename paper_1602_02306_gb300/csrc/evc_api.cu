@@ -1663,6 +1663,39 @@ int evc_get_tridiag(evc_ctx* ctx, double* alpha, double* beta, int* kdone)
     return EVC_OK;
 }
 
+int evc_get_quad_bound(evc_ctx* ctx, double* log10_bound)
+{
+    if (!ctx) return EVC_EINVAL;
+    if (!log10_bound) return fail(ctx, EVC_EINVAL, "null output");
+    if (!ctx->have_run) return fail(ctx, EVC_EINVAL, "no previous run");
+    const int K = ctx->run.kmax, nq = ctx->run.nq;
+    const double vn2 = (double)ctx->run.n;     // ||v||^2 of a Rademacher probe
+    std::vector<double> b((size_t)(K + 1) * nq);
+    std::vector<int> kd(nq);
+    const int rc = evc_get_tridiag(ctx, nullptr, b.data(), kd.data());
+    if (rc) return rc;
+    for (int c = 0; c < nq; ++c) {
+        const int k = kd[c];
+        if (k < 1) {
+            log10_bound[c] = std::nan("");
+            continue;
+        }
+        // log10 of ||v||^2 prod_{j=2}^{k+1} beta_j^2 / (2k)!
+        double s = std::log10(vn2) - std::lgamma(2.0 * k + 1.0) / std::log(10.0);
+        bool exact = false;
+        for (int j = 2; j <= k + 1; ++j) {
+            const double bj = b[(size_t)c * (K + 1) + (j - 1)];
+            if (!(bj > 0.0)) {
+                exact = true;
+                break;
+            }
+            s += 2.0 * std::log10(bj);
+        }
+        log10_bound[c] = exact ? -INFINITY : s;
+    }
+    return EVC_OK;
+}
+
 int evc_set_option(evc_ctx* ctx, int option, int64_t value)
 {
     if (!ctx) return EVC_EINVAL;

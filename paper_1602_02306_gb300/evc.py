@@ -47,7 +47,7 @@ EVC_MAX_STEPS = 256
 EXPORTED = [
     "evc_create_csr", "evc_create_stencil", "evc_set_values", "evc_set_precond",
     "evc_workspace_bytes", "evc_set_workspace", "evc_count", "evc_count_slices",
-    "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_set_option",
+    "evc_count_slices_async", "evc_sync", "evc_get_tridiag", "evc_get_quad_bound", "evc_set_option",
     "evc_get_profile", "evc_autotune", "evc_server_create", "evc_server_add_matrix", "evc_server_submit",
     "evc_server_poll", "evc_server_wait", "evc_server_stats", "evc_server_destroy",
     "evc_gauss_quadrature_static", "evc_wait_selftest", "evc_last_error", "evc_destroy",
@@ -121,6 +121,7 @@ def load(path: str | None = None):
             "evc_count_slices_async": (i32, [vp, dp, i32, i32, i32, d, u64, vp, vp, vp]),
             "evc_sync": (i32, [vp]),
             "evc_get_tridiag": (i32, [vp, dp, dp, ip]),
+            "evc_get_quad_bound": (i32, [vp, dp]),
             "evc_autotune": (i32, [vp, i32, i32, i32, C.POINTER(evc_tuning)]),
             "evc_wait_selftest": (i32, [d, C.POINTER(C.c_int)]),
             "evc_set_option": (i32, [vp, i32, i64]),
@@ -257,6 +258,12 @@ def evc_get_tridiag(ctx, ncol, maxsteps):
     kd = np.zeros(ncol, dtype=np.int32)
     _check(ctx, load().evc_get_tridiag(ctx, _dp(a), _dp(b), _ip(kd)))
     return a.reshape(ncol, maxsteps), b.reshape(ncol, maxsteps + 1), kd
+
+
+def evc_get_quad_bound(ctx, ncol):
+    out = np.zeros(ncol)
+    _check(ctx, load().evc_get_quad_bound(ctx, _dp(out)))
+    return out
 
 
 def evc_set_option(ctx, option, value):
@@ -443,6 +450,9 @@ class Context:
 
     def tridiag(self, ncol, maxsteps):
         return evc_get_tridiag(self.h, ncol, maxsteps)
+
+    def quad_bound(self, ncol):
+        return evc_get_quad_bound(self.h, ncol)
 
     def close(self):
         if self.h:

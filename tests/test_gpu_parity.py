@@ -119,6 +119,39 @@ def test_breakdown_at_p_distinct_eigenvalues():
             assert abs(q[0, j] - exact) < (1e-8 if prec == evc.EVC_FP64 else 1e-3)
 
 
+@pytest.mark.parametrize("prec_kind", [evc.EVC_PREC_IDENTITY, evc.EVC_PREC_JACOBI])
+def test_quad_bound_diagnostic_matches_oracle(prec_kind):
+    # Sec. 3, Eq. qbound: the library's per-column log10(||v||^2 beta_2^2 ...
+    # beta_{k+1}^2 / (2k)!) against the oracle's factor on Algorithm 1's own
+    # tridiagonals (FP64), including columns cut short by the stop rule
+    A = I.random_symmetric_dense(300, seed=7)
+    A[np.abs(A) < 1.2] = 0.0
+    A = 0.5 * (A + A.T) + np.diag(np.linspace(-3, 3, 300))
+    csr = I.dense_to_csr(A)
+    shifts, m, k = [-1.0, 0.25], 37, 20
+    opk = O.PREC_NONE if prec_kind == evc.EVC_PREC_IDENTITY else O.PREC_JACOBI
+    P = O.Problem.csr_matrix(csr, opk)
+    with evc.Context.csr(csr, precision=evc.EVC_FP64) as ctx:
+        ctx.set_precond(prec_kind, 1e-3)
+        for tol in (0.0, 0.5):
+            ctx.count_slices(shifts, m, k, tol=tol, seed=0)
+            got = ctx.quad_bound(len(shifts) * m)
+            _, _, kd = ctx.tridiag(len(shifts) * m, k)
+            for c in (0, 5, 36, 37, 73):
+                s, j = divmod(c, m)
+                v = O.probe_vector(0, j, 300)
+                _, be, _, _ = O.lanczos(P, shifts[s], v, int(kd[c]))
+                assert got[c] == pytest.approx(O.quad_bound_log10(be, int(kd[c]), v @ v), abs=1e-8)
+            assert np.all(np.isfinite(got))
+    # p distinct eigenvalues: the process breaks down and the bound collapses
+    distinct = [-2.0, -0.5, 0.7, 1.5, 3.0]
+    D = I.random_symmetric_dense(64, seed=4, distinct=distinct)
+    with evc.Context.csr(I.dense_to_csr(D), precision=evc.EVC_FP64) as ctx:
+        ctx.count_slices([0.0], 4, 12, seed=0)
+        got = ctx.quad_bound(4)
+    assert np.all(got < -20.0)
+
+
 def test_edge_sizes():
     csr = I.laplace2d_dirichlet(5)          # n = 25
     P = O.Problem.csr_matrix(csr, O.PREC_NONE)
