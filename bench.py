@@ -456,6 +456,20 @@ def _fp64_leg(evc, W, args, stream, seed, ws_mixed, shifts=None):
             "quad": q}, None
 
 
+def _serving_extra(args, nreq=1000, low_nreq=250):
+    """A shorter serving run for the default line: nreq requests at the
+    offered rate, then low_nreq at the low rate (the full run is
+    `--workload serving`)."""
+    import torch
+    torch.cuda.empty_cache()
+    main, low, clk, _, budget = _serving_run(args, nreq, args.rate, low_nreq, args.low_rate)
+    return {"workload": f"serving_8x_fd_7pt_32^3-128^3_{args.serving_precond}",
+            "requests": nreq, "offered_rps": args.rate, "slots": args.slots,
+            "hbm_budget_GB": round(budget / 1e9, 1),
+            "value": round(main["probe_steps"] / main["span_s"], 1), "unit": UNIT,
+            "serving": main, "serving_low_rate": low, "clocks": clk}
+
+
 def _extra(evc, name, args, stream, peak, peak_kind, seed):
     """Another workload of the path, measured the same way, for the same line."""
     import torch
@@ -655,6 +669,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.extras:
         line["extra_workloads"] = {}
         for name in [x for x in args.extras.split(",") if x and x != args.workload]:
+            if name == "serving":
+                line["extra_workloads"][name] = _serving_extra(args)
+                continue
             line["extra_workloads"][name] = _extra(evc, name, args, stream, peak, peak_kind, seed)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -693,16 +710,15 @@ def cpu_baseline(W, nprobe_sample, seed=0):
             "seconds": round(dt, 2)}
 
 
-def run_serving(args):
-    """Serving workload: count requests on 8 resident FD Hamiltonians arriving
-    as a Poisson stream, served by the library's request server."""
+def _serving_run(args, nreq, rate, low_nreq, low_rate, rank=0):
+    """Count requests on 8 resident FD Hamiltonians arriving as a Poisson
+    stream, served by the library's request server: a phase of nreq requests
+    at `rate` per second (clocks sampled), then a lighter one (low_nreq at
+    low_rate; none when low_rate <= 0).  Returns (main, low, clocks, stats,
+    HBM budget)."""
     import torch
     from paper_1602_02306_gb300 import evc, inputs
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    evc.load()
     Ns = [32, 40, 48, 64, 80, 96, 112, 128]
     h = 0.3
     ctxs, vmin = [], []
@@ -771,13 +787,29 @@ def run_serving(args):
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    main = phase(args.requests, args.rate, 3 + rank)
+    main = phase(nreq, rate, 3 + rank)
     clk = clocks.stop()
-    low = phase(args.low_requests, args.low_rate, 103 + rank) if args.low_rate > 0 else None
+    low = phase(low_nreq, low_rate, 103 + rank) if low_rate > 0 else None
     st = evc.evc_server_stats(srv)
     evc.evc_server_destroy(srv)
     for c in ctxs:
         c.close()
+    main = dict(main, peak_hbm_GB=round(st["peak_bytes"] / 1e9, 2))
+    return main, low, clk, st, budget
+
+
+def run_serving(args):
+    """Serving workload: count requests on 8 resident FD Hamiltonians arriving
+    as a Poisson stream, served by the library's request server."""
+    import torch
+    from paper_1602_02306_gb300 import evc
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    evc.load()
+    main, low, clk, st, budget = _serving_run(args, args.requests, args.rate, args.low_requests,
+                                              args.low_rate, rank)
     value = main["probe_steps"] / main["span_s"]
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.requests, "warmup": len(mids),
@@ -790,7 +822,7 @@ def run_serving(args):
                        "probes": [32, 64, 128], "tol": [0.25, 0.5], "maxsteps": 30,
                        "min_steps": 10, "precond": args.serving_precond,
                        "step": "one request (2 shifts x m probes, early stop)"},
-            "serving": dict(main, peak_hbm_GB=round(st["peak_bytes"] / 1e9, 2)),
+            "serving": main,
             "serving_low_rate": low,
             "clocks": clk,
             "e2e": {"value": round(value, 1), "unit": UNIT,
@@ -895,7 +927,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="powerlaw2m")
-    ap.add_argument("--extras", default="fd64,slicing96",
+    ap.add_argument("--extras", default="fd64,slicing96,serving",
                     help="other workloads measured for the same line (comma list, '' for none)")
     ap.add_argument("--extra-steps", type=int, default=3, help="timed counts per extra workload")
     ap.add_argument("--e2e-steps", type=int, default=5,
