@@ -1,7 +1,8 @@
 """Parity at the benchmark's full sizes, on sampled probes.
 
 The GPU runs the whole workload exactly as bench.py does (all shifts and
-probes in one batched launch); the FP64 oracle recomputes a sample of probe
+probes in one batched launch, in the tile shapes its autotuner picks on a
+GB300); the FP64 oracle recomputes a sample of probe
 columns one by one at full size, on all host cores.  FP64 mode: per-probe
 quadrature within 1e-8.  Mixed mode: per-probe quadrature within 0.5 and the
 sampled mean within 0.5 (the estimate tolerance).  With a tolerance-driven
@@ -33,7 +34,18 @@ def _lib():
     evc.load()
 
 
-def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS, tinv=0):
+# The tile shapes the library's autotuner picks for these workloads on a GB300
+# (the benchmark's launch configuration): tensor-copied 7-point tiles with four
+# chunk groups on 64^3, 13-point register patches on 96^3, 128-thread CSR blocks.
+BENCH_SHAPES = {
+    "fd64": {evc.EVC_OPT_STENCIL_PATCH: 3, evc.EVC_OPT_STENCIL_ZB: 32, evc.EVC_OPT_STENCIL_GROUPS: 4},
+    "slicing96": {evc.EVC_OPT_STENCIL_PATCH: 2, evc.EVC_OPT_STENCIL_ZB: 64,
+                  evc.EVC_OPT_STENCIL_GROUPS: 1},
+    "powerlaw2m": {evc.EVC_OPT_CSR_THREADS: 128},
+}
+
+
+def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS, tinv=0, shapes=None):
     import torch
     if W.kind == "stencil":
         ctx = evc.Context.stencil(W.N, W.h, W.order, W.potential(), precision=precision)
@@ -50,6 +62,8 @@ def _gpu(W, precision, method=evc.EVC_METHOD_LANCZOS, tinv=0):
         evc.evc_set_option(ctx.h, evc.EVC_OPT_MIN_STEPS, W.min_steps)
         evc.evc_set_option(ctx.h, evc.EVC_OPT_METHOD, method)
         evc.evc_set_option(ctx.h, evc.EVC_OPT_TINV_LANCZOS, tinv)
+        for opt, val in (shapes or {}).items():
+            evc.evc_set_option(ctx.h, opt, val)
         out = ctx.count_slices(W.shifts, W.nprobe, W.maxsteps, tol=W.tol, seed=0)
     torch.cuda.empty_cache()
     return out
@@ -77,8 +91,8 @@ def _sample_oracle(W, P, shift_idx, probe_ids, steps):
 
 def test_fd_hamiltonian_64_fullsize():
     W = workloads.fd_hamiltonian_64()
-    L64, q64, st64 = _gpu(W, evc.EVC_FP64)
-    Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED)
+    L64, q64, st64 = _gpu(W, evc.EVC_FP64, shapes=BENCH_SHAPES["fd64"])
+    Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED, shapes=BENCH_SHAPES["fd64"])
     assert list(st64) == list(stmx) == [W.maxsteps] * len(W.shifts)
     P = _oracle_problem(W)
     ids = [0, 13, 31, 40, 63]
@@ -93,8 +107,8 @@ def test_fd_hamiltonian_64_fullsize():
 @pytest.fixture(scope="module")
 def powerlaw_2m_runs():
     W = workloads.powerlaw_2m()
-    L64, q64, st64 = _gpu(W, evc.EVC_FP64)
-    Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED)
+    L64, q64, st64 = _gpu(W, evc.EVC_FP64, shapes=BENCH_SHAPES["powerlaw2m"])
+    Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED, shapes=BENCH_SHAPES["powerlaw2m"])
     return W, (L64, q64, st64), (Lmx, qmx, stmx)
 
 
@@ -144,7 +158,7 @@ def test_powerlaw_2m_tinv_lanczos_fullsize(powerlaw_2m_runs):
 
 def test_slicing_96_fullsize():
     W = workloads.batched_slicing_96()
-    Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED)
+    Lmx, qmx, stmx = _gpu(W, evc.EVC_MIXED, shapes=BENCH_SHAPES["slicing96"])
     assert all(W.min_steps <= s <= W.maxsteps for s in stmx)
     P = _oracle_problem(W)
     ids = [5, 50]
@@ -159,7 +173,7 @@ def test_slicing_96_fullsize():
     # compared with the same shift of the mixed run
     import dataclasses
     Wf = dataclasses.replace(W, shifts=[W.shifts[s] for s in shifts])
-    Lf, qf, stf = _gpu(Wf, evc.EVC_FP64)
+    Lf, qf, stf = _gpu(Wf, evc.EVC_FP64, shapes=BENCH_SHAPES["slicing96"])
     assert list(stf) == [int(stmx[s]) for s in shifts]
     for j, s in enumerate(shifts):
         assert abs(Lmx[s] - Lf[j]) < MIXED_TOL
