@@ -19,7 +19,10 @@
  *   - Output arrays are caller-allocated HOST memory unless stated.
  *   - A context owns one CUDA stream binding (the caller's stream, or the
  *     legacy default stream when NULL); calls on one context must not run
- *     concurrently from several host threads.
+ *     concurrently from several host threads.  This is deliberate: a
+ *     context's captured graph, workspace and pinned staging buffers are its
+ *     own state.  Concurrent callers use one context each (the request
+ *     server runs a clone of each matrix's context per slot).
  *   - Probes: v_j[i] = -1 if bit 63 of x is set, else +1, where
  *     x = mix(seed ^ mix((j << 32) | i)) and mix is the SplitMix64 output
  *     finaliser.  The same probes serve every shift of one call.
