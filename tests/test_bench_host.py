@@ -149,3 +149,33 @@ def test_early_stop_rates_split_at_the_first_stop():
     assert out["dots_all_running_GBps"] == pytest.approx(6000.0)
     assert out["dots_some_stopped_GBps"] == pytest.approx(3000.0)
     assert out["update_all_running_GBps"] is None       # untimed record only
+
+
+def test_quad_bound_summary_per_shift():
+    # per shift, the median and the largest of the per-probe Eq. qbound factors
+    class _E:
+        @staticmethod
+        def evc_get_quad_bound(h, ncol):
+            assert ncol == 6
+            return np.array([1.0, -3.0, 2.0, 10.0, 12.0, 11.0])
+
+    class _C:
+        h = None
+
+    class _W2:
+        shifts = [-0.5, 0.5]
+        nprobe = 3
+
+    out = bench._quad_bound_summary(_E, _C, _W2)
+    assert out["log10_median"] == [1.0, 11.0]
+    assert out["log10_max"] == [2.0, 12.0]
+
+
+def test_every_tracked_traffic_record_matches_its_device_code():
+    # a committed DRAM-traffic record is attached to a bench line only while
+    # the device code it was captured from is unchanged; every record in
+    # profiles/ must still match the sources (else it is stale)
+    import glob
+    for rec in glob.glob(os.path.join(ROOT, "profiles", "*_traffic.json")):
+        d = json.load(open(rec))
+        assert bench._device_code_sha(d["device_code"]) == d["device_code_sha256"], rec
